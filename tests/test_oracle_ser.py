@@ -1,0 +1,47 @@
+"""Uncoded symbol-error rate of the oracle's VP against ZF and MMSE (Section II).
+
+The paper's own error-rate curves are printed only as images, so their values
+are not available: this comparison is qualitative (parity with the paper's
+curves is unpinned). It checks the property the paper builds on: at the same
+transmit power, VP with the MoP candidate paths makes fewer symbol errors than
+the linear precoders on seeded i.i.d. Rayleigh channels.
+"""
+import numpy as np
+
+from paper_2602_12098_gb300 import workloads as W
+
+
+def ser_curves(orc, K, M, qam, n, snr_db, C=300, S=4, seed=60):
+    rng = W.rng_for(seed, K)
+    H = W.channels(rng, C, K, M)
+    sym = W.symbols(rng, C * S, K, qam)
+    off = np.arange(C + 1, dtype=np.int32) * S
+    tau = orc.default_tau(qam)
+    vp = orc.precode_batch(H, sym, off, qam, n)
+    sigma2 = 10 ** (-snr_db / 10)
+    es = orc.qam_energy(qam)
+    noise = (rng.standard_normal((C * S, K)) + 1j * rng.standard_normal((C * S, K))) * np.sqrt(sigma2 / 2)
+    err = {"vp": 0, "zf": 0, "mmse": 0}
+    for v in range(C * S):
+        Hc = H[v // S].astype(np.complex128)
+        s = orc.qam_points(qam, sym[v])
+        # VP: receiver scales by sqrt(gamma) (genie gamma) and applies mod_tau
+        y = Hc @ vp["x"][v] + noise[v]
+        err["vp"] += np.sum(orc.qam_slice(qam, orc.centered_mod(np.sqrt(vp["gamma"][v]) * y, tau)) != sym[v])
+        # ZF with per-vector normalisation
+        xz, gz = orc.zf_precode(Hc, s)
+        y = Hc @ xz + noise[v]
+        err["zf"] += np.sum(orc.qam_slice(qam, np.sqrt(gz) * y) != sym[v])
+        # MMSE with the expected-power normalisation of Eq. (gamm)
+        G = orc.mmse_matrix(Hc, sigma2 / 1.0)
+        gm = es * float(np.real(np.trace(G.conj().T @ G)))
+        y = Hc @ (G @ s) / np.sqrt(gm) + noise[v]
+        err["mmse"] += np.sum(orc.qam_slice(qam, np.sqrt(gm) * y) != sym[v])
+    tot = C * S * K
+    return {k: v / tot for k, v in err.items()}
+
+
+def test_vp_beats_linear_precoders(orc):
+    r = ser_curves(orc, K=4, M=4, qam=16, n=16, snr_db=22)
+    assert r["vp"] < 0.5 * r["zf"]
+    assert r["vp"] < r["mmse"]
