@@ -1,0 +1,167 @@
+/*
+ * libvp -- vector-perturbation (VP) precoding on one GB300 GPU (sm_103a).
+ *
+ * The library implements the data-parallel hot path of ViPer NL-COMM
+ * (Thomas, Katsaros, Jayawardena, Nikitopoulos, "ViPer NL-COMM: Making
+ * Vector Perturbation Precoding Practical", arXiv 2602.12098):
+ *
+ *   per channel (Alg. 2 "Regularize & factorize", lambda = 0, and
+ *   "Most Promising Perturbation Vector Identification"):
+ *     - the min-norm-first sorted RQ of H (Alg. 1 with the index reversal of
+ *       Section IV-B), H_perm = R Q, so (H H^H)^-1 = U^H U with U = R^-1
+ *       upper triangular (Eq. viper_rq1);
+ *     - the n_paths position vectors with the smallest Metric of Promise
+ *       (Eq. mop) by K-Best;
+ *   per data vector (Alg. 2 "Parallel post-processing"):
+ *     - every candidate path descends the K tree levels from level K, with
+ *       per-level interference cancellation and the p_l-th nearest Gaussian
+ *       integer around the effective point of Eq. (17) (DEMAP);
+ *     - the candidate with the smallest gamma = ||U (s + tau l)||^2 wins,
+ *       the zero perturbation being candidate 0 (ties: lower index);
+ *     - x = H^H (H H^H)^-1 (s + tau l) / sqrt(gamma)   (v_precoded, P_T = 1).
+ *
+ * Notation: K users (paper N_R), M AP antennas (paper N_T), s the QAM
+ * symbol vector (paper v), l = -t the perturbation (paper t), tau the
+ * perturbation interval. A "level" l = 0..K-1 is the paper's tree level l+1.
+ *
+ * Memory. Every array argument is caller-owned DEVICE memory unless marked
+ * HOST. Complex numbers are interleaved (re, im) float pairs (complex64),
+ * row-major. The plan owns only its resident per-channel state (factor,
+ * paths, precoding matrix) and frees it in vp_plan_destroy.
+ *
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream). Calls enqueue work and return without synchronising,
+ * except where noted.
+ *
+ * Errors. Argument errors are returned synchronously and nothing is
+ * enqueued. Launch failures return VP_ERR_CUDA. Per-channel numerical
+ * problems are reported in the `status` byte array (VP_CH_* bits); the
+ * outputs of such a channel are zero. No call aborts or traps.
+ *
+ * Threading. A plan is used by one host thread at a time. Different plans
+ * are independent.
+ */
+#ifndef VP_H
+#define VP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vp_plan vp_plan;
+
+typedef enum {
+    VP_OK = 0,
+    VP_ERR_INVALID_ARG = 1,    /* a size, pointer or parameter is out of range */
+    VP_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed */
+    VP_ERR_OOM = 3,            /* device allocation failed */
+    VP_ERR_TIMEOUT = 4,        /* a bounded device wait gave up */
+    VP_ERR_NOT_FACTORIZED = 5  /* vp_precode before vp_factorize, or for more channels */
+} vp_status;
+
+/* Per-channel status bits (the `status` output of vp_factorize). */
+#define VP_CH_NONFINITE 1u  /* H holds NaN or Inf; the channel's outputs are zero */
+#define VP_CH_SINGULAR  2u  /* a pivot fell below 1e-12 of the largest row norm^2 (rank deficient) */
+#define VP_CH_FP64      4u  /* kappa_hat exceeded the plan's threshold: factorised in FP64 */
+
+/* Largest supported sizes. */
+#define VP_MAX_K 16
+#define VP_MAX_M 16
+#define VP_MAX_PATHS 1024
+
+/*
+ * Create a plan for one problem shape.
+ *   K        users, 1 <= K <= VP_MAX_K
+ *   M        antennas, K <= M <= VP_MAX_M (lambda = 0 needs H H^H invertible)
+ *   qam      4, 16, 64 or 256; QAM index i maps to the odd-integer point
+ *            (2(i mod m) - (m-1)) + j(2 floor(i/m) - (m-1)), m = sqrt(qam)
+ *   n_paths  candidate paths, 1 <= n_paths <= min(9^K, VP_MAX_PATHS)
+ *   tau      perturbation interval > 0; pass 0 for the default 2*sqrt(qam)
+ *   out      HOST: receives the plan
+ * The FP64 fix-up threshold starts at kappa_hat > 1e4 (vp_plan_set_fp64_threshold).
+ * Allocates nothing on the device yet. Returns VP_ERR_INVALID_ARG on bad sizes.
+ */
+vp_status vp_plan_create(int K, int M, int qam, int n_paths, float tau, vp_plan** out);
+
+/* Channels whose kappa_hat = max_l R_ll^2 / min_l R_ll^2 (a lower bound on
+ * cond(H H^H)) exceeds `kappa_hat` are re-factorised in FP64 on the GPU
+ * (pivoted Cholesky of the FP64 Gram matrix and one Newton refinement of
+ * U). 0 sends every channel to FP64; +inf none. Negative or NaN is invalid. */
+vp_status vp_plan_set_fp64_threshold(vp_plan* plan, float kappa_hat);
+
+/* Free the plan and its device state. Synchronises the device first so that
+ * no enqueued work still reads the state. NULL is accepted. */
+vp_status vp_plan_destroy(vp_plan* plan);
+
+/*
+ * Factorise C channels and select their candidate paths (Alg. 1, Eq. mop,
+ * K-Best); the results stay resident in the plan for the vp_precode calls
+ * that follow (one slot: the 14 symbols share the channel).
+ *   H       complex64 [C][K][M], H[c][k][m] = channel from antenna m to user k
+ *   C       number of channels, C >= 1 (the plan grows its state as needed)
+ *   U       optional (may be NULL): complex64 [C][K][K], the upper factor
+ *           U = R^-1 in LEVEL order ((H_perm H_perm^H)^-1 = U^H U)
+ *   P       optional (may be NULL): complex64 [C][M][K], the precoding
+ *           matrix P = H^H (H H^H)^-1 in USER order (x = P u / sqrt(gamma))
+ *   user_of_level  optional (may be NULL): uint8 [C][K], the user at each level
+ *   status  optional (may be NULL): uint8 [C], VP_CH_* bits per channel
+ * Growing the plan allocates device memory (cudaMalloc) and synchronises.
+ */
+vp_status vp_factorize(vp_plan* plan, const void* H, int C, void* U, void* P,
+                       uint8_t* user_of_level, uint8_t* status, void* stream);
+
+/*
+ * Precode data vectors against the channels of the last vp_factorize.
+ *   sym_idx      uint8 [V][K], QAM indices in USER order
+ *   S            vectors per channel when vec_offsets is NULL (V = C*S,
+ *                vector v belongs to channel v / S)
+ *   vec_offsets  optional int32 [C+1]: channel c owns vectors
+ *                vec_offsets[c] .. vec_offsets[c+1]-1 (non-decreasing,
+ *                vec_offsets[0] = 0); then S is ignored and V = n_vec
+ *   n_vec        number of vectors V (must equal C*S when vec_offsets is NULL)
+ *   x            complex64 [V][M] precoded vectors, ||x|| = 1
+ *   l            int8 [V][K][2] perturbation (re, im) in USER order, entries in {-1,0,1}
+ *   gamma        float [V], gamma = ||U (s + tau l)||^2 of the chosen candidate
+ * Returns VP_ERR_NOT_FACTORIZED if no channels are resident.
+ */
+vp_status vp_precode(vp_plan* plan, const uint8_t* sym_idx, int S, const int32_t* vec_offsets,
+                     int n_vec, void* x, int8_t* l, float* gamma, void* stream);
+
+/*
+ * Copy the resident candidate paths of the last vp_factorize.
+ *   codes  uint64 [C][n_paths]: path k of channel c, rank order (smallest
+ *          Metric of Promise first, ties by code); 4 bits per level
+ *          (p_l - 1 at bits 4l..4l+3)
+ */
+vp_status vp_get_paths(vp_plan* plan, uint64_t* codes, void* stream);
+
+/*
+ * One whole slot from HOST buffers: copies H and sym_idx to the device,
+ * runs vp_factorize and vp_precode (S vectors per channel), copies x, l and
+ * gamma back, and waits for the stream. Host buffers should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for asynchronous copies; pageable
+ * memory works but copies synchronously.
+ *   H_host      HOST complex64 [C][K][M]
+ *   sym_host    HOST uint8 [C*S][K]
+ *   x_host      HOST complex64 [C*S][M]
+ *   l_host      HOST int8 [C*S][K][2] (may be NULL)
+ *   gamma_host  HOST float [C*S] (may be NULL)
+ * The plan keeps device staging buffers for these copies.
+ */
+vp_status vp_run_slot_host(vp_plan* plan, const void* H_host, int C, const uint8_t* sym_host,
+                           int S, void* x_host, int8_t* l_host, float* gamma_host, void* stream);
+
+/* Number of kernel launches the last vp_factorize / vp_precode /
+ * vp_run_slot_host call enqueued (copies and memsets not counted). */
+int vp_last_launch_count(const vp_plan* plan);
+
+/* Human-readable name of a status code (static string). */
+const char* vp_status_string(vp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VP_H */

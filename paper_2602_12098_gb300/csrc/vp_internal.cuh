@@ -1,0 +1,116 @@
+// Internal declarations of libvp (GPU side only; never included by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vp.h"
+
+namespace vp {
+
+constexpr int kMaxK = VP_MAX_K;
+constexpr int kMaxM = VP_MAX_M;
+constexpr int kMaxPaths = VP_MAX_PATHS;
+
+// Resident per-channel state of a plan (device pointers, capacity `cap` channels).
+struct DeviceState {
+    float4* utp = nullptr;     // [cap][K][K] unit-upper U~ = U_lk / U_ll, as (re, im, im, re)
+    float2* utc = nullptr;     // [cap][K][K] U~ transposed (utc[m][l] = U~[l][m]), for the per-vector prologue
+    float* w = nullptr;        // [cap][K]    w_l = U_ll^2 = 1 / R_ll^2
+    uint8_t* ul = nullptr;     // [cap][K]    user at level l
+    float2* pt = nullptr;      // [cap][K][M] P^T in user order: pt[c][k][m] = P[m][k] (leading part)
+    float2* ptlo = nullptr;    // [cap][K][M] trailing part: P = pt + ptlo (zero where P is FP32-accurate)
+    uint64_t* paths = nullptr; // [cap][n]    path codes, rank order
+    uint64_t* maxq = nullptr;  // [cap][nchunk] per 32-path chunk, per level: max digit (4 bits/level)
+    uint8_t* st = nullptr;     // [cap]       VP_CH_* bits
+    int* nflag = nullptr;      // [1]         number of channels sent to the FP64 path
+    int* flags = nullptr;      // [cap]       their indices
+};
+
+}  // namespace vp
+
+struct vp_plan {
+    int K = 0, M = 0, qam = 0, n_paths = 0;
+    float tau = 0.f;
+    float kappa_thr = 1e4f;
+    int cap = 0;   // channel capacity of `d`
+    int C = 0;     // channels of the last vp_factorize
+    vp::DeviceState d;
+    // staging buffers of vp_run_slot_host
+    void* h_H = nullptr; size_t h_H_bytes = 0;
+    uint8_t* h_sym = nullptr; size_t h_sym_bytes = 0;
+    void* h_x = nullptr; size_t h_x_bytes = 0;
+    int8_t* h_l = nullptr; size_t h_l_bytes = 0;
+    float* h_g = nullptr; size_t h_g_bytes = 0;
+    int last_launches = 0;
+};
+
+namespace vp {
+
+inline int n_chunks(int n_paths) { return (n_paths + 31) / 32; }
+
+// Kernel launchers (each returns cudaSuccess or the launch error).
+cudaError_t launch_factor32(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
+                            uint8_t* ul_out, cudaStream_t s);
+cudaError_t launch_factor64(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
+                            uint8_t* ul_out, cudaStream_t s);
+cudaError_t launch_pathsel(const vp_plan* p, int C, cudaStream_t s);
+cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int32_t* vec_off,
+                          int n_vec, float2* x, int8_t* l, float* gamma, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Small device helpers shared by the kernels of this library.
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul_conj_a(float2 a, float2 b)   // conj(a) * b
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c)  // a*b + c
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// Error-free transformations (Dekker / Knuth): a*b = p + e and a+b = s + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += a * b, with a*b formed exactly and the running sum compensated.
+__device__ __forceinline__ void dot2_acc(float a, float b, float& hi, float& lo)
+{
+    float p, e, s, f;
+    two_prod(a, b, p, e);
+    two_sum(hi, p, s, f);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, f));
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// QAM index -> odd-integer point (exact in float): m = sqrt(qam).
+__device__ __forceinline__ float2 qam_point(int idx, int m)
+{
+    return make_float2((float)(2 * (idx % m) - (m - 1)), (float)(2 * (idx / m) - (m - 1)));
+}
+
+}  // namespace vp

@@ -1,0 +1,338 @@
+// Parallel post-processing of Alg. 2: for each data vector, every candidate
+// path descends the tree from level K (Section II-B PED recursion) and the
+// best candidate gives l, gamma and the precoded vector x.
+//
+// Mapping: one block per channel (its factor, paths and P staged in shared
+// memory), one warp per data vector, one lane per candidate path (32 paths
+// per pass). Per lane the residuals r_m (m below the current level) live in
+// registers; choosing t_l at level l updates them column-wise,
+//   r_m -= U~_ml * tau * t_l,  m < l,
+// with two packed FP32 FMAs per complex term. The effective point of
+// Eq. (17) is s_hat_l = r_l / tau and t_l is its p_l-th nearest point of
+// {-1,0,1}+j{-1,0,1} (DEMAP), ties to the smaller (Re t, Im t).
+// The zero perturbation is candidate 0; the warp's (PED, index) minimum wins
+// (ties: lower index). x = P (s + tau l) / sqrt(gamma) with gamma = ||P u||^2,
+// the product P u formed with exact products and compensated sums.
+#include "vp_internal.cuh"
+
+namespace vp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SearchArgs {
+    const uint8_t* sym;
+    const int32_t* off;
+    int S, n_vec, C;
+    float2* x;
+    int8_t* l;
+    float* gamma;
+    int K, M, n, nch, m_qam;
+    float tau, inv_tau;
+    DeviceState d;
+};
+
+// Points of {-1,0,1} in increasing distance to c (ties to the smaller
+// coordinate), with their squared distances.
+struct Axis {
+    int n0, n1, n2;
+    float d0, d1, d2;
+};
+
+__device__ __forceinline__ Axis axis_order(float c)
+{
+    Axis a;
+    a.n0 = (c <= -0.5f) ? -1 : ((c > 0.5f) ? 1 : 0);
+    a.n1 = (a.n0 != 0) ? 0 : ((c <= 0.f) ? -1 : 1);
+    a.n2 = (a.n0 != 0) ? -a.n0 : -a.n1;
+    const float e0 = (float)a.n0 - c, e1 = (float)a.n1 - c, e2 = (float)a.n2 - c;
+    a.d0 = e0 * e0;
+    a.d1 = e1 * e1;
+    a.d2 = e2 * e2;
+    return a;
+}
+
+__device__ __forceinline__ int pick3(int j, int a0, int a1, int a2) { return j == 0 ? a0 : (j == 1 ? a1 : a2); }
+__device__ __forceinline__ float pick3f(int j, float a0, float a1, float a2) { return j == 0 ? a0 : (j == 1 ? a1 : a2); }
+
+// The q-th (0-based) nearest point to (cx, cy) of the 3x3 alphabet, exact
+// ranking by squared distance with ties to the smaller alphabet index
+// 3(tr+1)+(ti+1). In the frame of the per-axis orders the distances form a
+// 3x3 table with sorted rows and columns (cell (i,j) = point (x_i, y_j)),
+// so the next nearest point is always one of the <= 3 corner cells of the
+// cells taken so far. `mq` is the largest q of the warp at this level
+// (uniform), which selects the cheapest exact branch.
+__device__ __forceinline__ void select_point(const Axis& ax, const Axis& ay, int q, int mq, int& tr, int& ti)
+{
+    if (mq == 0) {
+        tr = ax.n0;
+        ti = ay.n0;
+        return;
+    }
+    if (mq <= 2) {
+        const float vA = ax.d1 + ay.d0, vB = ax.d0 + ay.d1;              // cells (1,0), (0,1)
+        const int iA = 3 * (ax.n1 + 1) + (ay.n0 + 1), iB = 3 * (ax.n0 + 1) + (ay.n1 + 1);
+        const bool aFirst = vA < vB || (vA == vB && iA < iB);
+        const float vC = aFirst ? ax.d2 + ay.d0 : ax.d0 + ay.d2;          // (2,0) or (0,2)
+        const int iC = aFirst ? 3 * (ax.n2 + 1) + (ay.n0 + 1) : 3 * (ax.n0 + 1) + (ay.n2 + 1);
+        const float vO = aFirst ? vB : vA;
+        const int iO = aFirst ? iB : iA;
+        const bool oFirst = vO < vC || (vO == vC && iO < iC);
+        int ci = 0, cj = 0;
+        if (q == 1) {
+            ci = aFirst ? 1 : 0;
+            cj = aFirst ? 0 : 1;
+        } else if (q == 2) {
+            if (oFirst) { ci = aFirst ? 0 : 1; cj = aFirst ? 1 : 0; }
+            else { ci = aFirst ? 2 : 0; cj = aFirst ? 0 : 2; }
+        }
+        tr = pick3(ci, ax.n0, ax.n1, ax.n2);
+        ti = pick3(cj, ay.n0, ay.n1, ay.n2);
+        return;
+    }
+    // general: take cells one by one from the corners of the taken set
+    int c0 = 1, c1 = 0, c2 = 0;   // cells taken in rows 0, 1, 2 ((0,0) is rank 0)
+    int ri = 0, rj = 0;
+    for (int step = 1; step <= mq; ++step) {
+        float bv = INFINITY;
+        int bidx = 99, brow = 0, bcol = 0;
+        if (c0 < 3) {
+            const float v = ax.d0 + pick3f(c0, ay.d0, ay.d1, ay.d2);
+            const int id = 3 * (ax.n0 + 1) + (pick3(c0, ay.n0, ay.n1, ay.n2) + 1);
+            if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 0; bcol = c0; }
+        }
+        if (c1 < c0) {
+            const float v = ax.d1 + pick3f(c1, ay.d0, ay.d1, ay.d2);
+            const int id = 3 * (ax.n1 + 1) + (pick3(c1, ay.n0, ay.n1, ay.n2) + 1);
+            if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 1; bcol = c1; }
+        }
+        if (c2 < c1) {
+            const float v = ax.d2 + pick3f(c2, ay.d0, ay.d1, ay.d2);
+            const int id = 3 * (ax.n2 + 1) + (pick3(c2, ay.n0, ay.n1, ay.n2) + 1);
+            if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 2; bcol = c2; }
+        }
+        if (step <= q) { ri = brow; rj = bcol; }
+        c0 += (brow == 0);
+        c1 += (brow == 1);
+        c2 += (brow == 2);
+    }
+    tr = pick3(ri, ax.n0, ax.n1, ax.n2);
+    ti = pick3(rj, ay.n0, ay.n1, ay.n2);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int K = a.K, M = a.M, n = a.n, nch = a.nch;
+    const int NW = blockDim.x >> 5;
+    float4* utp = reinterpret_cast<float4*>(smraw);                 // [KT][KT]
+    float2* utc = reinterpret_cast<float2*>(utp + KT * KT);        // [KT][KT]
+    float2* pt = utc + KT * KT;                                    // [K][M] leading part of P^T
+    float2* ptl = pt + K * M;                                      // [K][M] trailing part
+    float2* bvec = ptl + K * M;                                    // [NW][KT]
+    uint64_t* paths = reinterpret_cast<uint64_t*>(bvec + NW * KT); // [n]
+    uint64_t* maxq = paths + n;                                    // [nch]
+    float* wv = reinterpret_cast<float*>(maxq + nch);              // [KT]
+    int* ulv = reinterpret_cast<int*>(wv + KT);                    // [KT]
+
+    const int c = blockIdx.x;
+    int v0, v1;
+    if (a.off) {
+        v0 = min(max(a.off[c], 0), a.n_vec);
+        v1 = min(max(a.off[c + 1], v0), a.n_vec);
+    } else {
+        v0 = c * a.S;
+        v1 = v0 + a.S;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (a.d.st[c] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
+        for (int v = v0 + warp; v < v1; v += NW) {
+            if (lane < M) a.x[(size_t)v * M + lane] = make_float2(0.f, 0.f);
+            if (lane < K) {
+                a.l[((size_t)v * K + lane) * 2] = 0;
+                a.l[((size_t)v * K + lane) * 2 + 1] = 0;
+            }
+            if (lane == 0) a.gamma[v] = 0.f;
+        }
+        return;
+    }
+
+    for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
+        const int r = i / KT, q = i % KT;
+        const bool in = r < K && q < K;
+        utp[i] = in ? a.d.utp[((size_t)c * K + r) * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        utc[i] = in ? a.d.utc[((size_t)c * K + r) * K + q] : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < K * M; i += blockDim.x) {
+        pt[i] = a.d.pt[(size_t)c * K * M + i];
+        ptl[i] = a.d.ptlo[(size_t)c * K * M + i];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) paths[i] = a.d.paths[(size_t)c * n + i];
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) maxq[i] = a.d.maxq[(size_t)c * nch + i];
+    for (int i = threadIdx.x; i < KT; i += blockDim.x) {
+        wv[i] = i < K ? a.d.w[(size_t)c * K + i] : 0.f;
+        ulv[i] = i < K ? (int)a.d.ul[(size_t)c * K + i] : 0;
+    }
+    __syncthreads();
+
+    const float tau = a.tau, inv_tau = a.inv_tau;
+    float2* bw = bvec + warp * KT;
+    for (int v = v0 + warp; v < v1; v += NW) {
+        // symbols in level order (lane k <-> level k) and b_k = s_k + sum_{m>k} U~_km s_m
+        float2 s = make_float2(0.f, 0.f);
+        if (lane < K) s = qam_point((int)a.sym[(size_t)v * K + ulv[lane]], a.m_qam);
+        float2 b = s;
+        for (int m = 1; m < K; ++m) {
+            const float2 sm = make_float2(__shfl_sync(kFull, s.x, m), __shfl_sync(kFull, s.y, m));
+            if (lane < m) b = cfma(utc[m * KT + lane], sm, b);
+        }
+        if (lane < KT) bw[lane] = (lane < K) ? b : make_float2(0.f, 0.f);
+        float g0 = (lane < K) ? wv[lane] * cabs2(b) : 0.f;     // zero candidate: ||U s||^2
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) g0 += __shfl_xor_sync(kFull, g0, o);
+        __syncwarp(kFull);
+
+        float bp = INFINITY;
+        int bi = 0x7fffffff;
+        uint64_t blc = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int jp = ch * 32 + lane;
+            const bool vld = jp < n;
+            const uint64_t code = vld ? paths[jp] : 0ull;
+            const uint64_t mq = maxq[ch];
+            float2 r[KT];
+#pragma unroll
+            for (int m = 0; m < KT; ++m) r[m] = bw[m];
+            float ped = 0.f;
+            uint64_t lc = 0;
+#pragma unroll
+            for (int lv = KT - 1; lv >= 0; --lv) {
+                if (lv < K) {
+                    const int q = (int)((code >> (4 * lv)) & 15u);
+                    const int mql = (int)((mq >> (4 * lv)) & 15u);
+                    const Axis ax = axis_order(r[lv].x * inv_tau);
+                    const Axis ay = axis_order(r[lv].y * inv_tau);
+                    int tr, ti;
+                    select_point(ax, ay, q, mql, tr, ti);
+                    const float ftr = (float)tr * tau, fti = (float)ti * tau;
+                    const float dx = r[lv].x - ftr, dy = r[lv].y - fti;
+                    ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
+                    lc |= (uint64_t)((tr + 1) | ((ti + 1) << 2)) << (4 * lv);
+                    const float2 c1 = make_float2(-ftr, -ftr);
+                    const float2 c2 = make_float2(fti, -fti);
+#pragma unroll
+                    for (int m = 0; m < lv; ++m) {
+                        const float4 u = utp[m * KT + lv];
+                        r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
+                        r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
+                    }
+                }
+            }
+            if (vld && ped < bp) { bp = ped; bi = jp + 1; blc = lc; }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float obp = __shfl_xor_sync(kFull, bp, o);
+            const int obi = __shfl_xor_sync(kFull, bi, o);
+            if (obp < bp || (obp == bp && obi < bi)) { bp = obp; bi = obi; }
+        }
+        const bool zero_wins = !(bp < g0);
+        const int src = zero_wins ? 0 : ((bi - 1) & 31);
+        uint64_t wlc = __shfl_sync(kFull, blc, src);
+        if (zero_wins) wlc = 0x5555555555555555ull;
+
+        // l (user order) and u = s + tau l = s - tau t in level order
+        float2 u = make_float2(0.f, 0.f);
+        if (lane < K) {
+            const int nib = (int)((wlc >> (4 * lane)) & 15u);
+            const int tr = (nib & 3) - 1, ti = (nib >> 2) - 1;
+            u = make_float2(s.x - (float)tr * tau, s.y - (float)ti * tau);
+            const int usr = ulv[lane];
+            a.l[((size_t)v * K + usr) * 2] = (int8_t)(-tr);
+            a.l[((size_t)v * K + usr) * 2 + 1] = (int8_t)(-ti);
+        }
+        // y = P u with P = pt + ptl: exact products and compensated sums (u holds
+        // small integers, so P u keeps ~48 bits before the final rounding)
+        float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
+        for (int lv = 0; lv < K; ++lv) {
+            const float ur = __shfl_sync(kFull, u.x, lv), ui = __shfl_sync(kFull, u.y, lv);
+            if (lane < M) {
+                const int idx = ulv[lv] * M + lane;
+                const float2 ph = pt[idx], pl = ptl[idx];
+                dot2_acc(ph.x, ur, yr, yre);
+                dot2_acc(-ph.y, ui, yr, yre);
+                dot2_acc(ph.x, ui, yi, yie);
+                dot2_acc(ph.y, ur, yi, yie);
+                yre = fmaf(pl.x, ur, fmaf(-pl.y, ui, yre));
+                yie = fmaf(pl.x, ui, fmaf(pl.y, ur, yie));
+            }
+        }
+        const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
+        float g = (lane < M) ? cabs2(y) : 0.f;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
+        const float rs = __frsqrt_rn(g);
+        if (lane < M) a.x[(size_t)v * M + lane] = make_float2(y.x * rs, y.y * rs);
+        if (lane == 0) a.gamma[v] = g;
+        __syncwarp(kFull);
+    }
+}
+
+template <int KT>
+cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
+{
+    const int NW = threads / 32;
+    const size_t sh = sizeof(float4) * KT * KT + sizeof(float2) * KT * KT + 2 * sizeof(float2) * a.K * a.M +
+                      sizeof(float2) * NW * KT + sizeof(uint64_t) * (a.n + a.nch) + sizeof(float) * KT +
+                      sizeof(int) * KT;
+    static size_t attr = 0;
+    if (sh > 40 * 1024 && sh > attr) {
+        cudaError_t e = cudaFuncSetAttribute(search_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        attr = sh;
+    }
+    search_kernel<KT><<<C, threads, sh, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int32_t* vec_off, int n_vec,
+                          float2* x, int8_t* l, float* gamma, cudaStream_t s)
+{
+    SearchArgs a;
+    a.sym = sym;
+    a.off = vec_off;
+    a.S = S;
+    a.n_vec = n_vec;
+    a.C = p->C;
+    a.x = x;
+    a.l = l;
+    a.gamma = gamma;
+    a.K = p->K;
+    a.M = p->M;
+    a.n = p->n_paths;
+    a.nch = n_chunks(p->n_paths);
+    int m = 1;
+    while (m * m < p->qam) ++m;
+    a.m_qam = m;
+    a.tau = p->tau;
+    a.inv_tau = 1.0f / p->tau;
+    a.d = p->d;
+    // warps per block: a divisor-friendly count of the vectors per channel
+    const int per = vec_off ? (n_vec + p->C - 1) / p->C : S;
+    int nw = 8;
+    if (per <= 8) nw = per < 1 ? 1 : per;
+    else if (per % 7 == 0) nw = 7;
+    const int threads = nw * 32;
+    const int K = p->K;
+    if (K <= 2) return launch_kt<2>(a, p->C, threads, s);
+    if (K <= 4) return launch_kt<4>(a, p->C, threads, s);
+    if (K <= 8) return launch_kt<8>(a, p->C, threads, s);
+    if (K <= 12) return launch_kt<12>(a, p->C, threads, s);
+    return launch_kt<16>(a, p->C, threads, s);
+}
+
+}  // namespace vp

@@ -1,0 +1,183 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Sizes: the small 4x4 workload in full; the 8x8 per-RB and 16x16 slot
+workloads on reduced subcarrier counts (several tiles of 32 paths and a
+ragged vector tail) in full, and at their full sizes on sampled vectors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2602_12098_gb300 as vp
+from paper_2602_12098_gb300 import workloads as W
+from vp_gpu_util import assert_parity, compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vp.load()
+
+
+def oracle_run(orc, H, sym, off, qam, n, tau=None):
+    return orc.precode_batch(H, sym, off, qam, n, tau=tau, nthreads=orc.max_threads())
+
+
+def check_factor(orc, H, gpu, tol=2e-5):
+    """U (level order), user order and P against the oracle's Alg. 1 factor."""
+    C = H.shape[0]
+    order_ok = 0
+    for c in range(C):
+        f = orc.factor_channel(H[c].astype(np.complex128), 1)
+        if f["status"] != 0:
+            continue
+        if np.array_equal(gpu["ul"][c], f["user_of_level"]):
+            order_ok += 1
+            e = np.linalg.norm(gpu["U"][c] - f["Rt"]) / np.linalg.norm(f["Rt"])
+            assert e <= tol, (c, e)
+        Hc = H[c].astype(np.complex128)
+        eP = np.linalg.norm(gpu["P"][c] - np.linalg.pinv(Hc)) / np.linalg.norm(np.linalg.pinv(Hc))
+        assert eP <= tol, (c, eP)
+    assert order_ok >= 0.99 * C
+
+
+def test_small_4x4_full(orc):
+    b = W.make_batch(W.SMALL_4x4)
+    w = b.workload
+    gpu = run_gpu(b.H, b.sym, b.vec_off, w.qam, w.n_paths)
+    ref = oracle_run(orc, b.H, b.sym, b.vec_off, w.qam, w.n_paths)
+    assert np.all(gpu["status"] == 0)
+    check_factor(orc, b.H, gpu)
+    # candidate paths equal the oracle's MoP K-Best (rank order)
+    same = 0
+    for c in range(b.H.shape[0]):
+        f = orc.factor_channel(b.H[c].astype(np.complex128), w.n_paths)
+        same += int(np.array_equal(gpu["codes"][c], f["codes"]))
+    assert same >= 0.98 * b.H.shape[0]
+    st = compare(orc, b.H, b.sym, b.vec_off, w.qam, gpu, ref)
+    assert_parity(st)
+
+
+@pytest.mark.parametrize("K,M,qam,n", [(2, 2, 16, 81), (3, 3, 64, 729), (3, 4, 4, 729)])
+def test_all_paths_reach_exhaustive_minimum(orc, K, M, qam, n):
+    """n = 9^K: the GPU search covers every bounded perturbation, so its gamma
+    equals the oracle's exhaustive minimum."""
+    rng = W.rng_for(70, K * 10 + M)
+    C, S = 40, 3
+    H = W.channels(rng, C, K, M)
+    sym = W.symbols(rng, C * S, K, qam)
+    off = W.vec_offsets_uniform(C, S)
+    gpu = run_gpu(H, sym, off, qam, n)
+    tau = orc.default_tau(qam)
+    for v in range(C * S):
+        c = v // S
+        f = orc.factor_channel(H[c].astype(np.complex128), 1)
+        vl = orc.qam_points(qam, sym[v])[f["user_of_level"]]
+        g_bf, _ = orc.brute_min(f["Rt"], vl, tau)
+        assert abs(gpu["gamma"][v] - g_bf) <= 1e-5 * g_bf
+
+
+@pytest.mark.parametrize("wl,sub", [(W.RB_8x8, 24 * 12 + 6), (W.SLOT_16x16, 40)])
+def test_reduced_full_compare(orc, wl, sub):
+    b = W.make_batch(wl, subcarriers=sub)
+    gpu = run_gpu(b.H, b.sym, b.vec_off, wl.qam, wl.n_paths)
+    ref = oracle_run(orc, b.H, b.sym, b.vec_off, wl.qam, wl.n_paths)
+    assert np.array_equal(gpu["status"] & 3, ref["status"])
+    check_factor(orc, b.H, gpu)
+    st = compare(orc, b.H, b.sym, b.vec_off, wl.qam, gpu, ref)
+    print(wl.name, st)
+    assert_parity(st)
+
+
+@pytest.mark.parametrize("wl", [W.RB_8x8, W.SLOT_16x16])
+def test_full_size_sampled(orc, wl):
+    """Full-size launch (the benchmark's configuration); oracle on sampled vectors."""
+    b = W.make_batch(wl)
+    S = wl.symbols
+    gpu = run_gpu(b.H, b.sym, b.vec_off, wl.qam, wl.n_paths, want_factor=False,
+                  uniform_S=None if wl.per_rb else S)
+    C = b.H.shape[0]
+    rng = np.random.default_rng(5)
+    chans = np.sort(rng.choice(C, size=min(C, 48), replace=False))
+    vecs, off = [], [0]
+    for c in chans:
+        vv = np.arange(b.vec_off[c], b.vec_off[c + 1])
+        pick = vv if len(vv) <= 4 else rng.choice(vv, 4, replace=False)
+        vecs.extend(sorted(pick))
+        off.append(len(vecs))
+    vecs = np.asarray(vecs)
+    off = np.asarray(off, dtype=np.int32)
+    ref = oracle_run(orc, b.H[chans], b.sym[vecs], off, wl.qam, wl.n_paths)
+    sub = {k: gpu[k][vecs] for k in ("x", "l", "gamma")}
+    st = compare(orc, b.H[chans], b.sym[vecs], off, wl.qam, sub, ref)
+    print(wl.name, st)
+    assert_parity(st)
+    # properties at every vector: unit norm, |l| <= 1, gamma > 0
+    assert np.allclose(np.linalg.norm(gpu["x"], axis=1), 1.0, atol=1e-5)
+    assert np.all(np.abs(gpu["l"]) <= 1)
+    assert np.all(gpu["gamma"] > 0)
+
+
+def test_fp64_path_matches(orc):
+    """Every channel through the FP64 fix-up (threshold 0) still matches the oracle."""
+    b = W.make_batch(W.SLOT_16x16, subcarriers=24)
+    wl = b.workload
+    gpu = run_gpu(b.H, b.sym, b.vec_off, wl.qam, wl.n_paths, fp64_threshold=0.0)
+    assert np.all(gpu["status"] == vp.VP_CH_FP64)
+    check_factor(orc, b.H, gpu, tol=1e-6)
+    ref = oracle_run(orc, b.H, b.sym, b.vec_off, wl.qam, wl.n_paths)
+    assert_parity(compare(orc, b.H, b.sym, b.vec_off, wl.qam, gpu, ref))
+
+
+def test_edge_cases(orc):
+    rng = W.rng_for(71, 0)
+    # K = 1 (closed form), M > K, n not a multiple of 32, ragged per-channel vector counts
+    for K, M, qam, n in [(1, 1, 16, 9), (1, 3, 256, 5), (5, 7, 64, 45), (6, 6, 16, 100)]:
+        C = 7
+        H = W.channels(rng, C, K, M)
+        counts = rng.integers(0, 6, C)
+        off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        sym = W.symbols(rng, int(off[-1]), K, qam)
+        gpu = run_gpu(H, sym, off, qam, n)
+        ref = oracle_run(orc, H, sym, off, qam, n)
+        assert_parity(compare(orc, H, sym, off, qam, gpu, ref))
+    # identity channel (exact ties everywhere), a singular channel, a NaN channel
+    K = M = 4
+    H = W.channels(rng, 4, K, M)
+    H[0] = np.eye(4, dtype=np.complex64)
+    H[1, 3] = H[1, 0]
+    H[2, 1, 1] = np.nan
+    sym = W.symbols(rng, 8, K, 16)
+    off = W.vec_offsets_uniform(4, 2)
+    gpu = run_gpu(H, sym, off, 16, 16)
+    ref = oracle_run(orc, H, sym, off, 16, 16)
+    assert gpu["status"][1] & vp.VP_CH_SINGULAR and gpu["status"][2] == vp.VP_CH_NONFINITE
+    assert np.all(gpu["x"][2:6] == 0) and np.all(gpu["gamma"][2:6] == 0) and np.all(gpu["l"][2:6] == 0)
+    keep = np.r_[0:2, 6:8]
+    sub = {k: gpu[k][keep] for k in ("x", "l", "gamma")}
+    refk = {k: ref[k][keep] for k in ("x", "l", "gamma")}
+    st = compare(orc, H[[0, 3]], sym[keep], np.array([0, 2, 4], dtype=np.int32), 16, sub, refk)
+    assert st["n_l_diff"] == 0 and st["x_err_max"] <= 1e-6, st
+
+
+def test_host_buffer_slot_equals_device_path():
+    b = W.make_batch(W.SLOT_16x16, subcarriers=64)
+    wl = b.workload
+    S = wl.symbols
+    dev = run_gpu(b.H, b.sym, b.vec_off, wl.qam, wl.n_paths, want_factor=False, uniform_S=S)
+    C, K, M = b.H.shape
+    V = C * S
+    Hh = torch.from_numpy(b.H).pin_memory()
+    sh = torch.from_numpy(b.sym).pin_memory()
+    xh = torch.empty((V, M), dtype=torch.complex64).pin_memory()
+    lh = torch.empty((V, K, 2), dtype=torch.int8).pin_memory()
+    gh = torch.empty((V,), dtype=torch.float32).pin_memory()
+    with vp.Plan(K, M, wl.qam, wl.n_paths) as plan:
+        vp.vp_run_slot_host(plan.handle, Hh, C, sh, S, xh, lh, gh)
+        assert vp.vp_last_launch_count(plan.handle) == 4
+    assert np.array_equal(xh.numpy(), dev["x"])
+    assert np.array_equal(lh.numpy(), dev["l"])
+    assert np.array_equal(gh.numpy().astype(np.float64), dev["gamma"])
