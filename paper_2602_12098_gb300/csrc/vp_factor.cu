@@ -8,10 +8,11 @@
 //   Orthogonal reflections keep the error near FP32 rounding (the Gram
 //   matrix route squares the condition number). One half-warp per channel,
 //   lane j holds column j of A in registers.
-// factor64_kernel: channels whose kappa_hat = max R_ll^2 / min R_ll^2 passes
-//   the plan threshold are redone in FP64: Gram matrix, pivoted reverse
-//   Cholesky with the same min-pivot rule, U = R^-1 plus one Newton step
-//   U <- U (2I - R U), and P = H^H U^H U.
+// factor64_kernel: channels whose estimated cond(H H^H) (power iteration on R
+//   and U) passes the plan threshold are redone with FP64: the Gram matrix
+//   (compensated FP32 sums, exact for FP32 input), pivoted reverse Cholesky
+//   with the same min-pivot rule, U = R^-1 and one Newton step
+//   U <- U (2I - R U) in FP64, then P = H^H U^H U as a hi/lo FP32 pair.
 //
 // Outputs per channel (level order unless noted): U~ = U_lk / U_ll (unit
 // upper), w_l = U_ll^2, the user of each level, and P^T in user order.
@@ -22,7 +23,6 @@ namespace {
 
 constexpr int kLanes = 16;        // lanes per channel
 constexpr int kChPerBlock32 = 4;  // FP32 kernel: 64 threads
-constexpr int kChPerBlock64 = 2;  // FP64 kernel: 32 threads
 constexpr unsigned kFull = 0xffffffffu;
 
 struct FactorArgs {
@@ -65,6 +65,39 @@ __device__ __forceinline__ void write_channel_outputs_zero(const FactorArgs& a, 
         a.d.ul[(size_t)c * K + j] = (uint8_t)j;
         if (a.ul_out) a.ul_out[(size_t)c * K + j] = (uint8_t)j;
     }
+}
+
+// sigma_max(A)^2 of an upper-triangular K x K matrix held in shared memory,
+// by power iteration on A^H A (a lower bound that converges from below). Every
+// lane of the warp calls it; lane j < K holds component j of the iterate.
+__device__ float power_sigma2(const float2 (*A)[kMaxK], int K, int j)
+{
+    const bool act = j < K;
+    float2 v = make_float2(act ? 1.f + 0.0625f * (float)j : 0.f, 0.f);
+    float lam = 0.f;
+    for (int it = 0; it < 6; ++it) {
+        float2 w = make_float2(0.f, 0.f);                       // w = A v
+        for (int k = 0; k < K; ++k) {
+            const float2 vk = make_float2(__shfl_sync(kFull, v.x, k, kLanes), __shfl_sync(kFull, v.y, k, kLanes));
+            if (act && k >= j) w = cfma(A[j][k], vk, w);
+        }
+        float2 z = make_float2(0.f, 0.f);                       // z = A^H w
+        for (int i = 0; i < K; ++i) {
+            const float2 wi = make_float2(__shfl_sync(kFull, w.x, i, kLanes), __shfl_sync(kFull, w.y, i, kLanes));
+            if (act && i <= j) z = cfma(make_float2(A[i][j].x, -A[i][j].y), wi, z);
+        }
+        float nw = cabs2(w), nv = cabs2(v), nz = cabs2(z);
+#pragma unroll
+        for (int off = 8; off >= 1; off >>= 1) {
+            nw += __shfl_xor_sync(kFull, nw, off, kLanes);
+            nv += __shfl_xor_sync(kFull, nv, off, kLanes);
+            nz += __shfl_xor_sync(kFull, nz, off, kLanes);
+        }
+        lam = nw / nv;                                          // Rayleigh quotient of A^H A
+        const float sc = rsqrtf(nz);
+        v = make_float2(z.x * sc, z.y * sc);
+    }
+    return lam;
 }
 
 template <int MT>
@@ -167,34 +200,6 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     }
     __syncwarp(kFull);
 
-    // kappa_hat = (max R_ll / min R_ll)^2 and the FP64 decision
-    float rmax = act ? sm.rdiag[j] : 0.f;
-    float rmin = act ? sm.rdiag[j] : INFINITY;
-#pragma unroll
-    for (int off = 8; off >= 1; off >>= 1) {
-        rmax = fmaxf(rmax, __shfl_xor_sync(kFull, rmax, off, kLanes));
-        rmin = fminf(rmin, __shfl_xor_sync(kFull, rmin, off, kLanes));
-    }
-    const bool degen = (__ballot_sync(kFull, degenerate) & hmask) != 0u;
-    const float ratio = rmax / rmin;
-    const float kappa = ratio * ratio;
-    const bool to64 = !nonfinite && (degen || !(kappa <= a.kappa_thr));
-    if (!valid) return;
-
-    if (nonfinite) {
-        write_channel_outputs_zero(a, c, j);
-        if (j == 0) a.d.st[c] = (uint8_t)VP_CH_NONFINITE;
-        return;
-    }
-    if (to64) {
-        if (j == 0) {
-            const int idx = atomicAdd(a.d.nflag, 1);
-            a.d.flags[idx] = c;
-            a.d.st[c] = (uint8_t)VP_CH_FP64;
-        }
-        return;
-    }
-
     // R in level order: level i <-> step K-1-i
     if (act) {
         const int i = j;
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
             sm.rl[i][k] = v;
         }
     }
-    __syncwarp(hmask);
+    __syncwarp(kFull);
 
     // U = R^-1, lane k computes column k by back substitution
     if (act) {
@@ -225,7 +230,28 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
         }
         for (int i = k + 1; i < K; ++i) sm.uu[i][k] = make_float2(0.f, 0.f);
     }
-    __syncwarp(hmask);
+    __syncwarp(kFull);
+
+    // cond(H H^H) = (sigma_max(R) sigma_max(U))^2, estimated by power iteration;
+    // channels above the plan threshold (or degenerate) go to the FP64 path
+    const float kappa = power_sigma2(sm.rl, K, j) * power_sigma2(sm.uu, K, j);
+    const bool degen = (__ballot_sync(kFull, degenerate) & hmask) != 0u;
+    const bool to64 = !nonfinite && (degen || !(kappa <= a.kappa_thr));
+    if (!valid) return;
+
+    if (nonfinite) {
+        write_channel_outputs_zero(a, c, j);
+        if (j == 0) a.d.st[c] = (uint8_t)VP_CH_NONFINITE;
+        return;
+    }
+    if (to64) {
+        if (j == 0) {
+            const int idx = atomicAdd(a.d.nflag, 1);
+            a.d.flags[idx] = c;
+            a.d.st[c] = (uint8_t)VP_CH_FP64;
+        }
+        return;
+    }
 
     if (act) {
         const int i = j;
@@ -283,175 +309,200 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 }
 
 // ---------------------------------------------------------------------------
-// FP64 path for the flagged channels.
+// FP64 path for the flagged channels: one 256-thread block per channel,
+// thread (r, q) <-> matrix entry (r, q). GB300's FP64 rate is low, so FP64 is
+// kept to the pivoted Cholesky of the Gram matrix, U = R^-1 and one Newton
+// step; the Gram matrix and P are accumulated in compensated FP32 (exact
+// products of the FP32 inputs, ~48-bit sums).
 
 struct Smem64 {
-    float2 h[kMaxK][kMaxM];
-    double2 s[kMaxK][kMaxK];     // Schur complement (user index); later the refined U
-    double2 lc[kMaxK][kMaxK];    // lc[t][j] = S[j][p] / R_tt at level t; later E and A
-    double2 r[kMaxK][kMaxK];     // R, level order
+    float2 h[kMaxK][kMaxM];      // H rows (user order)
+    double2 s[kMaxK][kMaxK];     // Gram / Schur complement, lower triangle (user index); later A = U2^H U2
+    double2 lc[kMaxK][kMaxK];    // lc[t][j]: column of R at level t, by user j; later the substitution sums
+    double2 r[kMaxK][kMaxK];     // R, level order; later E = I - R U
     double2 u[kMaxK][kMaxK];     // U = R^-1
+    double2 u2[kMaxK][kMaxK];    // U after one Newton step
+    double2 pc[kMaxK];           // pivot column / R_tt of the current step
     double rd[kMaxK];
     int uol[kMaxK];
+    double dmax;
+    double pivv;
+    int piv;
 };
 
-__global__ void __launch_bounds__(kLanes * kChPerBlock64) factor64_kernel(FactorArgs a)
+__device__ __forceinline__ double2 s_at(const Smem64& sm, int i, int j)   // Schur entry (i, j) from the lower triangle
 {
-    __shared__ Smem64 smem[kChPerBlock64];
-    const int half = threadIdx.x / kLanes;
-    const int j = threadIdx.x % kLanes;
-    Smem64& sm = smem[half];
+    return i >= j ? sm.s[i][j] : zconj(sm.s[j][i]);
+}
+
+__global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
+{
+    __shared__ Smem64 sm;
+    const int tid = threadIdx.x;
+    const int r = tid >> 4, q = tid & 15;
     const int K = a.K, M = a.M;
     const int nflag = *a.d.nflag;
 
-    for (int base = blockIdx.x * kChPerBlock64; base < nflag; base += gridDim.x * kChPerBlock64) {
-        const int slot = base + half;
-        const bool on = slot < nflag;
-        const int c = on ? a.d.flags[slot] : 0;
-
-        if (on && j < K)
-            for (int m = 0; m < M; ++m) sm.h[j][m] = a.H[((size_t)c * K + j) * M + m];
-        __syncwarp(kFull);
-        if (on && j < K) {
-            for (int i = 0; i < K; ++i) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int m = 0; m < M; ++m) {
-                    const float2 x = sm.h[j][m], y = sm.h[i][m];
-                    acc = zfma(make_double2(x.x, x.y), make_double2(y.x, -(double)y.y), acc);
-                }
-                sm.s[j][i] = acc;
+    for (int slot = blockIdx.x; slot < nflag; slot += gridDim.x) {
+        const int c = a.d.flags[slot];
+        for (int i = tid; i < K * M; i += blockDim.x) sm.h[i / M][i % M] = a.H[(size_t)c * K * M + i];
+        __syncthreads();
+        // Gram, lower triangle: G_rq = sum_m h_rm conj(h_qm), compensated FP32 -> FP64
+        if (r < K && q <= r) {
+            float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
+            for (int m = 0; m < M; ++m) {
+                const float2 x = sm.h[r][m], y = sm.h[q][m];
+                dot2_acc(x.x, y.x, re, ree);
+                dot2_acc(x.y, y.y, re, ree);
+                dot2_acc(x.y, y.x, im, ime);
+                dot2_acc(-x.x, y.y, im, ime);
             }
+            sm.s[r][q] = make_double2((double)re + (double)ree, (double)im + (double)ime);
         }
-        __syncwarp(kFull);
+        __syncthreads();
+        if (tid == 0) {
+            double dm = 0.0;
+            for (int j = 0; j < K; ++j) dm = fmax(dm, sm.s[j][j].x);
+            sm.dmax = dm;
+        }
 
-        double dmax = (on && j < K) ? sm.s[j][j].x : 0.0;
-#pragma unroll
-        for (int off = 8; off >= 1; off >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, off, kLanes));
-
+        // pivoted reverse Cholesky: at level t (from K-1 down) the remaining user
+        // with the smallest Schur diagonal (ties: lowest user) becomes the pivot
         unsigned remm = (1u << K) - 1u;
         bool singular = false;
-        for (int t = K - 1; t >= 0; --t) {
-            // every lane of both halves runs every step (shuffles use the full mask)
-            double key = (on && !singular && ((remm >> j) & 1u)) ? sm.s[j][j].x : INFINITY;
-            int kj = j;
+        for (int t = K - 1; t >= 0 && !singular; --t) {
+            __syncthreads();
+            if (tid < 32) {
+                double key = (tid < K && ((remm >> tid) & 1u)) ? sm.s[tid][tid].x : INFINITY;
+                int kj = tid;
 #pragma unroll
-            for (int off = 8; off >= 1; off >>= 1) {
-                const double ok = __shfl_xor_sync(kFull, key, off, kLanes);
-                const int oj = __shfl_xor_sync(kFull, kj, off, kLanes);
-                if (ok < key || (ok == key && oj < kj)) { key = ok; kj = oj; }
+                for (int off = 16; off >= 1; off >>= 1) {
+                    const double ok = __shfl_xor_sync(kFull, key, off);
+                    const int oj = __shfl_xor_sync(kFull, kj, off);
+                    if (ok < key || (ok == key && oj < kj)) { key = ok; kj = oj; }
+                }
+                if (tid == 0) { sm.piv = kj; sm.pivv = key; }
             }
-            const int p = kj;
-            if (!(key > 1e-12 * dmax)) singular = true;             // uniform within the half
-            const double rt = sqrt(key);
+            __syncthreads();
+            const int p = sm.piv;
+            const double pv = sm.pivv;
+            if (!(pv > 1e-12 * sm.dmax)) { singular = true; break; }   // uniform: every thread reads the same values
+            const double rt = sqrt(pv);
             remm &= ~(1u << p);
-            if (!singular && j == p) { sm.rd[t] = rt; sm.uol[t] = p; }
-            if (on && !singular && ((remm >> j) & 1u)) {
-                const double2 v = sm.s[j][p];
-                sm.lc[t][j] = make_double2(v.x / rt, v.y / rt);
-            }
-            __syncwarp(kFull);
-            if (on && !singular && ((remm >> j) & 1u)) {
-                const double2 lj = sm.lc[t][j];
-                for (int i = 0; i < K; ++i) {
-                    if ((remm >> i) & 1u) {
-                        const double2 li = sm.lc[t][i];
-                        const double2 pr = zmul(lj, zconj(li));
-                        sm.s[j][i].x -= pr.x;
-                        sm.s[j][i].y -= pr.y;
-                    }
+            if (tid < K) {
+                double2 v = make_double2(0.0, 0.0);
+                if ((remm >> tid) & 1u) {
+                    const double2 sp = s_at(sm, tid, p);
+                    v = make_double2(sp.x / rt, sp.y / rt);
                 }
+                sm.pc[tid] = v;
+                sm.lc[t][tid] = v;
             }
-            __syncwarp(kFull);
+            if (tid == 0) { sm.rd[t] = rt; sm.uol[t] = p; }
+            __syncthreads();
+            if (r < K && q <= r && ((remm >> r) & 1u) && ((remm >> q) & 1u)) {
+                const double2 pr = zmul(sm.pc[r], zconj(sm.pc[q]));
+                sm.s[r][q].x -= pr.x;
+                sm.s[r][q].y -= pr.y;
+            }
         }
-        // the two halves may disagree on `singular`; each handles its own channel
-        const bool good = on && !singular;
+        __syncthreads();
 
-        if (good && j < K) {
-            const int i = j;
-            const int ui = sm.uol[i];
-            for (int k = 0; k < K; ++k)
-                sm.r[i][k] = (k > i) ? sm.lc[k][ui] : (k == i ? make_double2(sm.rd[i], 0.0) : make_double2(0.0, 0.0));
-        }
-        __syncwarp(kFull);
-        if (good && j < K) {                      // U = R^-1 (column j)
-            const int k = j;
-            sm.u[k][k] = make_double2(1.0 / sm.r[k][k].x, 0.0);
-            for (int i = k - 1; i >= 0; --i) {
-                double2 s = make_double2(0.0, 0.0);
-                for (int m = i + 1; m <= k; ++m) s = zfma(sm.r[i][m], sm.u[m][k], s);
-                sm.u[i][k] = make_double2(-s.x / sm.r[i][i].x, -s.y / sm.r[i][i].x);
-            }
-            for (int i = k + 1; i < K; ++i) sm.u[i][k] = make_double2(0.0, 0.0);
-        }
-        __syncwarp(kFull);
-        if (good && j < K) {                      // E = I - R U (column j), into lc
-            const int k = j;
-            for (int i = 0; i < K; ++i) {
-                double2 s = make_double2(i == k ? 1.0 : 0.0, 0.0);
-                for (int m = i; m <= k; ++m) {
-                    const double2 pr = zmul(sm.r[i][m], sm.u[m][k]);
-                    s.x -= pr.x;
-                    s.y -= pr.y;
+        if (!singular) {
+            // R in level order
+            if (r < K && q < K)
+                sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
+            __syncthreads();
+            // U = R^-1 by rows from the bottom: U_i. = (e_i - sum_{m>i} R_im U_m.) / R_ii
+            if (r < K && q < K) sm.lc[r][q] = make_double2(0.0, 0.0);
+            __syncthreads();
+            for (int m = K - 1; m >= 0; --m) {
+                if (tid < K) {
+                    const int k = tid;
+                    const double2 acc = sm.lc[m][k];
+                    const double rmm = sm.r[m][m].x;
+                    sm.u[m][k] = (k < m) ? make_double2(0.0, 0.0)
+                                         : make_double2(((k == m ? 1.0 : 0.0) - acc.x) / rmm, -acc.y / rmm);
                 }
-                sm.lc[i][k] = (i <= k) ? s : make_double2(0.0, 0.0);
+                __syncthreads();
+                if (r < m && q < K && q >= m) sm.lc[r][q] = zfma(sm.r[r][m], sm.u[m][q], sm.lc[r][q]);
+                __syncthreads();
             }
-        }
-        __syncwarp(kFull);
-        if (good && j < K) {                      // U2 = U + U E (Newton step), into s
-            const int k = j;
-            for (int i = 0; i < K; ++i) {
-                double2 s = sm.u[i][k];
-                for (int m = i; m <= k; ++m) s = zfma(sm.u[i][m], sm.lc[m][k], s);
-                sm.s[i][k] = (i <= k) ? s : make_double2(0.0, 0.0);
-            }
-        }
-        __syncwarp(kFull);
-        if (good && j < K) {                      // A = U2^H U2 (column j), into lc
-            const int k = j;
-            for (int i = 0; i < K; ++i) {
-                double2 s = make_double2(0.0, 0.0);
-                const int mx = i < k ? i : k;
-                for (int m = 0; m <= mx; ++m) s = zfma(zconj(sm.s[m][i]), sm.s[m][k], s);
-                sm.lc[i][k] = s;
-            }
-        }
-        __syncwarp(kFull);
-        if (good && j < K) {
-            const int i = j;                      // row i of U~, w_i, user of level i
-            const double uii = sm.s[i][i].x;
-            a.d.w[(size_t)c * K + i] = (float)(uii * uii);
-            const uint8_t ui = (uint8_t)sm.uol[i];
-            a.d.ul[(size_t)c * K + i] = ui;
-            if (a.ul_out) a.ul_out[(size_t)c * K + i] = ui;
-            for (int k = 0; k < K; ++k) {
-                const double2 u = sm.s[i][k];
-                const float2 ut = (k > i) ? make_float2((float)(u.x / uii), (float)(u.y / uii))
-                                          : (k == i ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
-                a.d.utp[((size_t)c * K + i) * K + k] = make_float4(ut.x, ut.y, ut.y, ut.x);
-                a.d.utc[((size_t)c * K + k) * K + i] = ut;
-                if (a.U_out) a.U_out[((size_t)c * K + i) * K + k] = make_float2((float)u.x, (float)u.y);
-            }
-            // P_level[:, k=j] = H_perm^H A[:, k]; stored under user uol[k]
-            const int k = j;
-            const int uk = sm.uol[k];
-            for (int m = 0; m < M; ++m) {
-                double2 s = make_double2(0.0, 0.0);
-                for (int q = 0; q < K; ++q) {
-                    const float2 hv = sm.h[sm.uol[q]][m];
-                    s = zfma(make_double2(hv.x, -(double)hv.y), sm.lc[q][k], s);
+            // one Newton step: E = I - R U, U2 = U + U E (upper triangular)
+            double2 e = make_double2(0.0, 0.0);
+            if (r < K && q < K && q >= r) {
+                e = make_double2(r == q ? 1.0 : 0.0, 0.0);
+                for (int m = r; m <= q; ++m) {
+                    const double2 pr = zmul(sm.r[r][m], sm.u[m][q]);
+                    e.x -= pr.x;
+                    e.y -= pr.y;
                 }
-                const float2 pv = make_float2((float)s.x, (float)s.y);
-                a.d.pt[((size_t)c * K + uk) * M + m] = pv;
-                a.d.ptlo[((size_t)c * K + uk) * M + m] =
-                    make_float2((float)(s.x - (double)pv.x), (float)(s.y - (double)pv.y));
-                if (a.P_out) a.P_out[((size_t)c * M + m) * K + uk] = pv;
             }
+            __syncthreads();
+            if (r < K && q < K) sm.r[r][q] = e;
+            __syncthreads();
+            if (r < K && q < K) {
+                double2 v = make_double2(0.0, 0.0);
+                if (q >= r) {
+                    v = sm.u[r][q];
+                    for (int m = r; m <= q; ++m) v = zfma(sm.u[r][m], sm.r[m][q], v);
+                }
+                sm.u2[r][q] = v;
+            }
+            __syncthreads();
+            // A = U2^H U2 (Hermitian), into s
+            if (r < K && q < K) {
+                double2 v = make_double2(0.0, 0.0);
+                const int mx = r < q ? r : q;
+                for (int m = 0; m <= mx; ++m) v = zfma(zconj(sm.u2[m][r]), sm.u2[m][q], v);
+                sm.s[r][q] = v;
+            }
+            __syncthreads();
+            // outputs: row r of U~, w_r, user of level r
+            if (r < K && q < K) {
+                const double urr = sm.u2[r][r].x;
+                const double2 uv = sm.u2[r][q];
+                const float2 ut = (q > r) ? make_float2((float)(uv.x / urr), (float)(uv.y / urr))
+                                          : (q == r ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
+                a.d.utp[((size_t)c * K + r) * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
+                a.d.utc[((size_t)c * K + q) * K + r] = ut;
+                if (a.U_out) a.U_out[((size_t)c * K + r) * K + q] = make_float2((float)uv.x, (float)uv.y);
+                if (q == 0) {
+                    a.d.w[(size_t)c * K + r] = (float)(urr * urr);
+                    a.d.ul[(size_t)c * K + r] = (uint8_t)sm.uol[r];
+                    if (a.ul_out) a.ul_out[(size_t)c * K + r] = (uint8_t)sm.uol[r];
+                }
+            }
+            // P_level[m][k] = sum_j conj(H_perm[j][m]) A[j][k], compensated FP32 with A = hi + lo
+            for (int e2 = tid; e2 < M * K; e2 += blockDim.x) {
+                const int m = e2 / K, k = e2 % K;
+                float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
+                for (int j = 0; j < K; ++j) {
+                    const float2 hv = sm.h[sm.uol[j]][m];
+                    const double2 av = sm.s[j][k];
+                    const float ahx = (float)av.x, ahy = (float)av.y;
+                    const float alx = (float)(av.x - (double)ahx), aly = (float)(av.y - (double)ahy);
+                    // conj(h) * a = (h.x a.x + h.y a.y) + i (h.x a.y - h.y a.x)
+                    dot2_acc(hv.x, ahx, re, ree);
+                    dot2_acc(hv.y, ahy, re, ree);
+                    dot2_acc(hv.x, ahy, im, ime);
+                    dot2_acc(-hv.y, ahx, im, ime);
+                    ree = fmaf(hv.x, alx, fmaf(hv.y, aly, ree));
+                    ime = fmaf(hv.x, aly, fmaf(-hv.y, alx, ime));
+                }
+                const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
+                const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
+                const int uk = sm.uol[k];
+                a.d.pt[((size_t)c * K + uk) * M + m] = hi;
+                a.d.ptlo[((size_t)c * K + uk) * M + m] = lo;
+                if (a.P_out) a.P_out[((size_t)c * M + m) * K + uk] = hi;
+            }
+            if (tid == 0) a.d.st[c] = (uint8_t)VP_CH_FP64;
+        } else {
+            if (tid < 16) write_channel_outputs_zero(a, c, tid);
+            if (tid == 0) a.d.st[c] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
         }
-        if (on && !good) {
-            write_channel_outputs_zero(a, c, j);
-        }
-        if (on && j == 0) a.d.st[c] = (uint8_t)(VP_CH_FP64 | (good ? 0u : VP_CH_SINGULAR));
-        __syncwarp(kFull);
+        __syncthreads();
     }
 }
 
@@ -488,9 +539,8 @@ cudaError_t launch_factor64(const vp_plan* p, const float2* H, int C, float2* U_
                             uint8_t* ul_out, cudaStream_t s)
 {
     const FactorArgs a = make_args(p, H, C, U_out, P_out, ul_out);
-    int blocks = (C + kChPerBlock64 - 1) / kChPerBlock64;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    factor64_kernel<<<blocks, kLanes * kChPerBlock64, 0, s>>>(a);
+    int blocks = C < 152 * 8 ? C : 152 * 8;
+    factor64_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -2,15 +2,19 @@
 // with the smallest Metric of Promise M(p) = sum_l w_l (p_l - 1) (Eq. mop),
 // by breadth-first K-Best over the levels.
 //
-// One block per channel. The weights are turned into integers
-// q_l = round(w_l / max_l w_l * 2^40), so every partial metric is an exact
-// uint64 sum and the order (metric, code) is a strict total order. With it,
-// K-Best keeps exactly the n smallest vectors, whatever the level order.
+// One block per channel. The weights are scaled by a power of two into
+// integers, q_l = w_l * 2^(55-e) with max_l w_l < 2^e (exact for every FP32
+// weight within 2^32 of the largest), so every partial metric is an exact
+// uint64 sum, ties in the real metric stay ties, and (metric, code) is a
+// strict total order. With it K-Best keeps exactly the n smallest vectors,
+// whatever the level order.
 //
-// Level step: the survivors S (sorted) spawn children S + k*q_l, k = 1..8.
-// Only children below the current n-th survivor can enter. Their ranks among
-// themselves come from binary searches in the 8 shifted copies of S (each
-// copy is sorted), and one merge-path pass merges them into S.
+// Level step: the children of the survivors S are S + k (q_l, 1 << 4l),
+// k = 0..8, all shifted copies of the sorted list S. Their n smallest follow
+// from three doubling merges and one more (S+{0,1} -> S+{0..3} -> S+{0..7},
+// then with S+8), each cut to n entries: the n smallest of a union only need
+// the n smallest of each part. A merge is skipped when the shifted copy
+// starts after the current n-th entry. Each merge is a merge-path pass.
 #include "vp_internal.cuh"
 
 namespace vp {
@@ -28,10 +32,11 @@ __device__ __forceinline__ bool key_less(uint64_t am, uint64_t ac, uint64_t bm, 
     return am < bm || (am == bm && ac < bc);
 }
 
-// First `nout` outputs of the merge of sorted A[0..na) and B[0..nb) into O.
-__device__ void merge_path(const uint64_t* Am, const uint64_t* Ac, int na,
-                           const uint64_t* Bm, const uint64_t* Bc, int nb,
-                           uint64_t* Om, uint64_t* Oc, int nout, int tid, int T)
+// First `nout` outputs of the merge of sorted A[0..na) with the sorted list
+// B[0..nb) shifted by (dm, dc), into O. Threads split the output range.
+__device__ void merge_shift(const uint64_t* Am, const uint64_t* Ac, int na,
+                            const uint64_t* Bm, const uint64_t* Bc, int nb, uint64_t dm, uint64_t dc,
+                            uint64_t* Om, uint64_t* Oc, int nout, int tid, int T)
 {
     const int per = (nout + T - 1) / T;
     const int d0 = min(tid * per, nout);
@@ -40,14 +45,15 @@ __device__ void merge_path(const uint64_t* Am, const uint64_t* Ac, int na,
     int lo = max(0, d0 - nb), hi = min(d0, na);
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (key_less(Am[mid], Ac[mid], Bm[d0 - mid - 1], Bc[d0 - mid - 1])) lo = mid + 1;
+        const int bj = d0 - mid - 1;
+        if (key_less(Am[mid], Ac[mid], Bm[bj] + dm, Bc[bj] + dc)) lo = mid + 1;
         else hi = mid;
     }
     int i = lo, j = d0 - lo;
     for (int d = d0; d < d1; ++d) {
-        const bool takeA = (j >= nb) || (i < na && key_less(Am[i], Ac[i], Bm[j], Bc[j]));
+        const bool takeA = (j >= nb) || (i < na && key_less(Am[i], Ac[i], Bm[j] + dm, Bc[j] + dc));
         if (takeA) { Om[d] = Am[i]; Oc[d] = Ac[i]; ++i; }
-        else { Om[d] = Bm[j]; Oc[d] = Bc[j]; ++j; }
+        else { Om[d] = Bm[j] + dm; Oc[d] = Bc[j] + dc; ++j; }
     }
 }
 
@@ -55,15 +61,9 @@ __global__ void pathsel_kernel(PathArgs a)
 {
     extern __shared__ uint64_t shm[];
     __shared__ uint64_t qw[kMaxK];
-    __shared__ int cnt[9];
-    __shared__ int pre[10];
     const int n = a.n, K = a.K, T = blockDim.x, tid = threadIdx.x;
-    uint64_t* Sm = shm;
-    uint64_t* Sc = Sm + n;
-    uint64_t* Em = Sc + n;
-    uint64_t* Ec = Em + n;
-    uint64_t* Nm = Ec + n;
-    uint64_t* Nc = Nm + n;
+    uint64_t* bm[3] = {shm, shm + 2 * n, shm + 4 * n};       // metrics of the three buffers
+    uint64_t* bc[3] = {shm + n, shm + 3 * n, shm + 5 * n};   // codes
     const int c = blockIdx.x;
     uint64_t* out = a.d.paths + (size_t)c * n;
     uint64_t* mqo = a.d.maxq + (size_t)c * a.nch;
@@ -76,83 +76,40 @@ __global__ void pathsel_kernel(PathArgs a)
     if (tid == 0) {
         float wmax = 0.f;
         for (int l = 0; l < K; ++l) wmax = fmaxf(wmax, a.d.w[(size_t)c * K + l]);
+        int e;
+        frexpf(wmax, &e);                      // wmax < 2^e, so 8 K w 2^(55-e) < 2^62
         for (int l = 0; l < K; ++l)
-            qw[l] = __double2ull_rn((double)a.d.w[(size_t)c * K + l] / (double)wmax * 1099511627776.0);
-        Sm[0] = 0;
-        Sc[0] = 0;
+            qw[l] = __double2ull_rn(ldexp((double)a.d.w[(size_t)c * K + l], 55 - e));
+        bm[0][0] = 0;
+        bc[0][0] = 0;
     }
     __syncthreads();
 
-    int s = 1;
+    int iS = 0, s = 1;
     for (int l = 0; l < K; ++l) {
         const uint64_t q = qw[l];
-        const int sh4 = 4 * l;
-        if (tid >= 1 && tid <= 8) {
-            const int k = tid;
-            int ck;
-            if (s < n) {
-                ck = s;                                  // every child is a candidate
-            } else {
-                const uint64_t lim = Sm[n - 1];
-                const uint64_t kq = (uint64_t)k * q;
-                if (kq >= lim) {
-                    ck = 0;
-                } else {                                 // #{i : Sm[i] + kq < lim}
-                    const uint64_t th = lim - kq;
-                    int lo = 0, hi = n;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (Sm[mid] < th) lo = mid + 1; else hi = mid;
-                    }
-                    ck = lo;
-                }
-            }
-            cnt[k] = ck;
+        const uint64_t d1 = 1ull << (4 * l);
+        int ix = iS, nx = s;
+        for (int step = 0; step < 4; ++step) {
+            // steps 0..2: X + 2^step * delta; step 3: S + 8 * delta
+            const uint64_t mul = step < 3 ? (1ull << step) : 8ull;
+            const int ib = step < 3 ? ix : iS;
+            const int nb = step < 3 ? nx : s;
+            const uint64_t dm = mul * q, dc = mul * d1;
+            const bool skip = nx >= n && key_less(bm[ix][n - 1], bc[ix][n - 1], bm[ib][0] + dm, bc[ib][0] + dc);
+            if (skip) continue;
+            const int io = (ix == iS) ? (iS + 1) % 3 : 3 - ix - iS;
+            const int nout = min(nx + nb, n);
+            merge_shift(bm[ix], bc[ix], nx, bm[ib], bc[ib], nb, dm, dc, bm[io], bc[io], nout, tid, T);
+            __syncthreads();
+            ix = io;
+            nx = nout;
         }
-        __syncthreads();
-        if (tid == 0) {
-            pre[1] = 0;
-            for (int k = 1; k <= 8; ++k) pre[k + 1] = pre[k] + cnt[k];
-        }
-        __syncthreads();
-        const int E = pre[9];
-        if (E == 0) continue;                            // no child enters: digit 0 everywhere
-
-        for (int e = tid; e < E; e += T) {
-            int k = 1;
-            while (e >= pre[k + 1]) ++k;
-            const int i = e - pre[k];
-            const uint64_t em = Sm[i] + (uint64_t)k * q;
-            const uint64_t ec = Sc[i];
-            int rank = i;
-            for (int k2 = 1; k2 <= 8; ++k2) {
-                const int len = cnt[k2];
-                if (k2 == k || len == 0) continue;
-                const uint64_t sq = (uint64_t)k2 * q;
-                int lo = 0, hi = len;
-                while (lo < hi) {                        // count children (j, k2) before (i, k)
-                    const int mid = (lo + hi) >> 1;
-                    const uint64_t mm = Sm[mid] + sq;
-                    const bool lt = mm < em || (mm == em && (k2 < k || (k2 == k && Sc[mid] < ec)));
-                    if (lt) lo = mid + 1; else hi = mid;
-                }
-                rank += lo;
-            }
-            if (rank < n) {
-                Em[rank] = em;
-                Ec[rank] = ec | ((uint64_t)k << sh4);
-            }
-        }
-        __syncthreads();
-        const int ne = E < n ? E : n;
-        const int outn = (s + ne) < n ? (s + ne) : n;
-        merge_path(Sm, Sc, s, Em, Ec, ne, Nm, Nc, outn, tid, T);
-        __syncthreads();
-        uint64_t* t0 = Sm; Sm = Nm; Nm = t0;
-        uint64_t* t1 = Sc; Sc = Nc; Nc = t1;
-        s = outn;
+        iS = ix;
+        s = nx;
     }
 
+    const uint64_t* Sc = bc[iS];
     for (int i = tid; i < n; i += T) out[i] = (i < s) ? Sc[i] : 0;
     const int warp = tid >> 5, lane = tid & 31;
     for (int ch = warp; ch < a.nch; ch += T >> 5) {

@@ -5,11 +5,13 @@
 // Mapping: one block per channel (its factor, paths and P staged in shared
 // memory), one warp per data vector, one lane per candidate path (32 paths
 // per pass). Per lane the residuals r_m (m below the current level) live in
-// registers; choosing t_l at level l updates them column-wise,
-//   r_m -= U~_ml * tau * t_l,  m < l,
-// with two packed FP32 FMAs per complex term. The effective point of
-// Eq. (17) is s_hat_l = r_l / tau and t_l is its p_l-th nearest point of
-// {-1,0,1}+j{-1,0,1} (DEMAP), ties to the smaller (Re t, Im t).
+// registers in units of tau (r' = r / tau is the effective point s_hat_l of
+// Eq. (17)); choosing t_l at level l updates them column-wise,
+//   r'_m -= U~_ml t_l,  m < l,
+// with two packed FP32 FMAs per complex term (skipped when every lane of the
+// warp chose t_l = 0), and t_l is the p_l-th nearest point of
+// {-1,0,1}+j{-1,0,1} to r'_l (DEMAP), ties to the smaller (Re t, Im t).
+// The PED grows by w_l tau^2 |r'_l - t_l|^2.
 // The zero perturbation is candidate 0; the warp's (PED, index) minimum wins
 // (ties: lower index). x = P (s + tau l) / sqrt(gamma) with gamma = ||P u||^2,
 // the product P u formed with exact products and compensated sums.
@@ -32,82 +34,80 @@ struct SearchArgs {
     DeviceState d;
 };
 
-// Points of {-1,0,1} in increasing distance to c (ties to the smaller
-// coordinate), with their squared distances.
+// DEMAP selection. Per axis the points of {-1,0,1} ordered by distance to
+// the coordinate c (ties to the smaller point) are n0, n1, n2 = -sg, with
+// n0 the rounding of c, sg = +1 for c > 0 else -1, n1 = sg if n0 = 0 else 0;
+// relative to n0 their squared distances grow by D1 = |1 - 2|c||
+// and D2 = max(1 + 2|c|, 4|c|). The 9 points form a 3x3 table of sums
+// Dx_i + Dy_j with sorted rows and columns (cell (i, j) = point (x_i, y_j)),
+// so the next nearest point is always a corner of the cells taken so far.
+// Exact ties go to the smaller alphabet index 3(tr+1) + (ti+1), i.e. to the
+// lexicographically smaller (tr, ti).
 struct Axis {
     int n0, n1, n2;
-    float d0, d1, d2;
+    float D1, D2;
 };
+
+__device__ __forceinline__ int round3(float c) { return (c > 0.5f) - (c <= -0.5f); }
 
 __device__ __forceinline__ Axis axis_order(float c)
 {
     Axis a;
-    a.n0 = (c <= -0.5f) ? -1 : ((c > 0.5f) ? 1 : 0);
-    a.n1 = (a.n0 != 0) ? 0 : ((c <= 0.f) ? -1 : 1);
-    a.n2 = (a.n0 != 0) ? -a.n0 : -a.n1;
-    const float e0 = (float)a.n0 - c, e1 = (float)a.n1 - c, e2 = (float)a.n2 - c;
-    a.d0 = e0 * e0;
-    a.d1 = e1 * e1;
-    a.d2 = e2 * e2;
+    a.n0 = round3(c);
+    const int sg = (c > 0.f) ? 1 : -1;
+    a.n1 = (a.n0 == 0) ? sg : 0;
+    a.n2 = -sg;
+    const float m = fabsf(c);
+    a.D1 = fabsf(fmaf(-2.f, m, 1.f));
+    a.D2 = fmaxf(fmaf(2.f, m, 1.f), 4.f * m);
     return a;
 }
 
 __device__ __forceinline__ int pick3(int j, int a0, int a1, int a2) { return j == 0 ? a0 : (j == 1 ? a1 : a2); }
 __device__ __forceinline__ float pick3f(int j, float a0, float a1, float a2) { return j == 0 ? a0 : (j == 1 ? a1 : a2); }
 
-// The q-th (0-based) nearest point to (cx, cy) of the 3x3 alphabet, exact
-// ranking by squared distance with ties to the smaller alphabet index
-// 3(tr+1)+(ti+1). In the frame of the per-axis orders the distances form a
-// 3x3 table with sorted rows and columns (cell (i,j) = point (x_i, y_j)),
-// so the next nearest point is always one of the <= 3 corner cells of the
-// cells taken so far. `mq` is the largest q of the warp at this level
-// (uniform), which selects the cheapest exact branch.
-__device__ __forceinline__ void select_point(const Axis& ax, const Axis& ay, int q, int mq, int& tr, int& ti)
+// q in {0, 1, 2}: rank 1 is (n1x, n0y) or (n0x, n1y); rank 2 is the other one
+// or the next point along the axis already used.
+__device__ __forceinline__ void select_q2(float cx, float cy, int q, int& tr, int& ti)
 {
-    if (mq == 0) {
-        tr = ax.n0;
-        ti = ay.n0;
-        return;
+    const Axis ax = axis_order(cx), ay = axis_order(cy);
+    // lexicographic tie-breaks: the two candidates differ in Re t, so compare it
+    const bool aFirst = ax.D1 < ay.D1 || (ax.D1 == ay.D1 && ax.n1 < ax.n0);
+    const bool oFirst = aFirst ? (ay.D1 < ax.D2 || (ay.D1 == ax.D2 && ax.n0 < ax.n2))
+                               : (ax.D1 < ay.D2 || (ax.D1 == ay.D2 && ax.n1 < ax.n0));
+    int ci = 0, cj = 0;
+    if (q == 1) {
+        ci = aFirst ? 1 : 0;
+        cj = aFirst ? 0 : 1;
+    } else if (q == 2) {
+        ci = aFirst ? (oFirst ? 0 : 2) : (oFirst ? 1 : 0);
+        cj = aFirst ? (oFirst ? 1 : 0) : (oFirst ? 0 : 2);
     }
-    if (mq <= 2) {
-        const float vA = ax.d1 + ay.d0, vB = ax.d0 + ay.d1;              // cells (1,0), (0,1)
-        const int iA = 3 * (ax.n1 + 1) + (ay.n0 + 1), iB = 3 * (ax.n0 + 1) + (ay.n1 + 1);
-        const bool aFirst = vA < vB || (vA == vB && iA < iB);
-        const float vC = aFirst ? ax.d2 + ay.d0 : ax.d0 + ay.d2;          // (2,0) or (0,2)
-        const int iC = aFirst ? 3 * (ax.n2 + 1) + (ay.n0 + 1) : 3 * (ax.n0 + 1) + (ay.n2 + 1);
-        const float vO = aFirst ? vB : vA;
-        const int iO = aFirst ? iB : iA;
-        const bool oFirst = vO < vC || (vO == vC && iO < iC);
-        int ci = 0, cj = 0;
-        if (q == 1) {
-            ci = aFirst ? 1 : 0;
-            cj = aFirst ? 0 : 1;
-        } else if (q == 2) {
-            if (oFirst) { ci = aFirst ? 0 : 1; cj = aFirst ? 1 : 0; }
-            else { ci = aFirst ? 2 : 0; cj = aFirst ? 0 : 2; }
-        }
-        tr = pick3(ci, ax.n0, ax.n1, ax.n2);
-        ti = pick3(cj, ay.n0, ay.n1, ay.n2);
-        return;
-    }
-    // general: take cells one by one from the corners of the taken set
+    tr = pick3(ci, ax.n0, ax.n1, ax.n2);
+    ti = pick3(cj, ay.n0, ay.n1, ay.n2);
+}
+
+// any q: walk the corners of the taken cells `mq` times (mq uniform, >= q)
+__device__ __noinline__ void select_general(float cx, float cy, int q, int mq, int& tr, int& ti)
+{
+    const Axis ax = axis_order(cx), ay = axis_order(cy);
     int c0 = 1, c1 = 0, c2 = 0;   // cells taken in rows 0, 1, 2 ((0,0) is rank 0)
     int ri = 0, rj = 0;
     for (int step = 1; step <= mq; ++step) {
         float bv = INFINITY;
         int bidx = 99, brow = 0, bcol = 0;
         if (c0 < 3) {
-            const float v = ax.d0 + pick3f(c0, ay.d0, ay.d1, ay.d2);
+            const float v = pick3f(c0, 0.f, ay.D1, ay.D2);
             const int id = 3 * (ax.n0 + 1) + (pick3(c0, ay.n0, ay.n1, ay.n2) + 1);
             if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 0; bcol = c0; }
         }
         if (c1 < c0) {
-            const float v = ax.d1 + pick3f(c1, ay.d0, ay.d1, ay.d2);
+            const float v = ax.D1 + pick3f(c1, 0.f, ay.D1, ay.D2);
             const int id = 3 * (ax.n1 + 1) + (pick3(c1, ay.n0, ay.n1, ay.n2) + 1);
             if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 1; bcol = c1; }
         }
         if (c2 < c1) {
-            const float v = ax.d2 + pick3f(c2, ay.d0, ay.d1, ay.d2);
+            const float v = ax.D2 + pick3f(c2, 0.f, ay.D1, ay.D2);
             const int id = 3 * (ax.n2 + 1) + (pick3(c2, ay.n0, ay.n1, ay.n2) + 1);
             if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 2; bcol = c2; }
         }
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
     for (int i = threadIdx.x; i < n; i += blockDim.x) paths[i] = a.d.paths[(size_t)c * n + i];
     for (int i = threadIdx.x; i < nch; i += blockDim.x) maxq[i] = a.d.maxq[(size_t)c * nch + i];
     for (int i = threadIdx.x; i < KT; i += blockDim.x) {
-        wv[i] = i < K ? a.d.w[(size_t)c * K + i] : 0.f;
+        wv[i] = i < K ? a.d.w[(size_t)c * K + i] * a.tau * a.tau : 0.f;   // w_l tau^2
         ulv[i] = i < K ? (int)a.d.ul[(size_t)c * K + i] : 0;
     }
     __syncthreads();
@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
             const float2 sm = make_float2(__shfl_sync(kFull, s.x, m), __shfl_sync(kFull, s.y, m));
             if (lane < m) b = cfma(utc[m * KT + lane], sm, b);
         }
+        // residuals are kept in units of tau: r' = r / tau is the effective point of Eq. (17)
+        b = make_float2(b.x * inv_tau, b.y * inv_tau);
         if (lane < KT) bw[lane] = (lane < K) ? b : make_float2(0.f, 0.f);
         float g0 = (lane < K) ? wv[lane] * cabs2(b) : 0.f;     // zero candidate: ||U s||^2
 #pragma unroll
@@ -196,41 +198,53 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
 
         float bp = INFINITY;
         int bi = 0x7fffffff;
-        uint64_t blc = 0;
+        uint32_t blc0 = 0, blc1 = 0;
         for (int ch = 0; ch < nch; ++ch) {
             const int jp = ch * 32 + lane;
             const bool vld = jp < n;
             const uint64_t code = vld ? paths[jp] : 0ull;
+            const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
             const uint64_t mq = maxq[ch];
+            const uint32_t mq0 = (uint32_t)mq, mq1 = (uint32_t)(mq >> 32);
             float2 r[KT];
 #pragma unroll
             for (int m = 0; m < KT; ++m) r[m] = bw[m];
             float ped = 0.f;
-            uint64_t lc = 0;
+            uint32_t lc0 = 0, lc1 = 0;
 #pragma unroll
             for (int lv = KT - 1; lv >= 0; --lv) {
                 if (lv < K) {
-                    const int q = (int)((code >> (4 * lv)) & 15u);
-                    const int mql = (int)((mq >> (4 * lv)) & 15u);
-                    const Axis ax = axis_order(r[lv].x * inv_tau);
-                    const Axis ay = axis_order(r[lv].y * inv_tau);
+                    const int sh = 4 * (lv & 7);
+                    const int q = (int)(((lv < 8) ? cw0 : cw1) >> sh) & 15;
+                    const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
+                    const float cx = r[lv].x, cy = r[lv].y;
                     int tr, ti;
-                    select_point(ax, ay, q, mql, tr, ti);
-                    const float ftr = (float)tr * tau, fti = (float)ti * tau;
-                    const float dx = r[lv].x - ftr, dy = r[lv].y - fti;
+                    if (mql == 0) {
+                        tr = round3(cx);
+                        ti = round3(cy);
+                    } else if (mql <= 2) {
+                        select_q2(cx, cy, q, tr, ti);
+                    } else {
+                        select_general(cx, cy, q, mql, tr, ti);
+                    }
+                    const float ftr = (float)tr, fti = (float)ti;
+                    const float dx = cx - ftr, dy = cy - fti;
                     ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
-                    lc |= (uint64_t)((tr + 1) | ((ti + 1) << 2)) << (4 * lv);
-                    const float2 c1 = make_float2(-ftr, -ftr);
-                    const float2 c2 = make_float2(fti, -fti);
+                    const uint32_t dig = (uint32_t)((tr + 1) | ((ti + 1) << 2)) << sh;
+                    if (lv < 8) lc0 |= dig; else lc1 |= dig;
+                    if (lv > 0 && (lv < 4 || __any_sync(kFull, (tr | ti) != 0))) {
+                        const float2 c1 = make_float2(-ftr, -ftr);
+                        const float2 c2 = make_float2(fti, -fti);
 #pragma unroll
-                    for (int m = 0; m < lv; ++m) {
-                        const float4 u = utp[m * KT + lv];
-                        r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
-                        r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
+                        for (int m = 0; m < lv; ++m) {
+                            const float4 u = utp[m * KT + lv];
+                            r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
+                            r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
+                        }
                     }
                 }
             }
-            if (vld && ped < bp) { bp = ped; bi = jp + 1; blc = lc; }
+            if (vld && ped < bp) { bp = ped; bi = jp + 1; blc0 = lc0; blc1 = lc1; }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -240,13 +254,13 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
         }
         const bool zero_wins = !(bp < g0);
         const int src = zero_wins ? 0 : ((bi - 1) & 31);
-        uint64_t wlc = __shfl_sync(kFull, blc, src);
-        if (zero_wins) wlc = 0x5555555555555555ull;
+        uint32_t w0 = __shfl_sync(kFull, blc0, src), w1 = __shfl_sync(kFull, blc1, src);
+        if (zero_wins) { w0 = 0x55555555u; w1 = 0x55555555u; }
 
         // l (user order) and u = s + tau l = s - tau t in level order
         float2 u = make_float2(0.f, 0.f);
         if (lane < K) {
-            const int nib = (int)((wlc >> (4 * lane)) & 15u);
+            const int nib = (int)(((lane < 8 ? w0 : w1) >> (4 * (lane & 7))) & 15u);
             const int tr = (nib & 3) - 1, ti = (nib >> 2) - 1;
             u = make_float2(s.x - (float)tr * tau, s.y - (float)ti * tau);
             const int usr = ulv[lane];

@@ -87,8 +87,14 @@ def test_reduced_full_compare(orc, wl, sub):
     ref = oracle_run(orc, b.H, b.sym, b.vec_off, wl.qam, wl.n_paths)
     assert np.array_equal(gpu["status"] & 3, ref["status"])
     check_factor(orc, b.H, gpu)
+    # candidate paths: the oracle's MoP K-Best on the same channel (rank order)
+    same = 0
+    for c in range(b.H.shape[0]):
+        f = orc.factor_channel(b.H[c].astype(np.complex128), wl.n_paths)
+        same += int(np.array_equal(gpu["codes"][c], f["codes"]))
+    assert same >= 0.95 * b.H.shape[0], same
     st = compare(orc, b.H, b.sym, b.vec_off, wl.qam, gpu, ref)
-    print(wl.name, st)
+    print(wl.name, st, "fp64 channels:", int(np.sum(gpu["status"] == vp.VP_CH_FP64)))
     assert_parity(st)
 
 
