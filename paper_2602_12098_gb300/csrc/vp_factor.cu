@@ -322,8 +322,11 @@ struct Smem64 {
     double2 r[kMaxK][kMaxK];     // R, level order; later E = I - R U
     double2 u[kMaxK][kMaxK];     // U = R^-1
     double2 u2[kMaxK][kMaxK];    // U after one Newton step
+    float2 ahi[kMaxK][kMaxK];    // A = U2^H U2 split into FP32 hi + lo
+    float2 alo[kMaxK][kMaxK];
     double2 pc[kMaxK];           // pivot column / R_tt of the current step
     double rd[kMaxK];
+    double rinv[kMaxK];          // 1 / R_mm
     int uol[kMaxK];
     double dmax;
     double pivv;
@@ -388,12 +391,13 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
             const double pv = sm.pivv;
             if (!(pv > 1e-12 * sm.dmax)) { singular = true; break; }   // uniform: every thread reads the same values
             const double rt = sqrt(pv);
+            const double irt = 1.0 / rt;
             remm &= ~(1u << p);
             if (tid < K) {
                 double2 v = make_double2(0.0, 0.0);
                 if ((remm >> tid) & 1u) {
                     const double2 sp = s_at(sm, tid, p);
-                    v = make_double2(sp.x / rt, sp.y / rt);
+                    v = make_double2(sp.x * irt, sp.y * irt);
                 }
                 sm.pc[tid] = v;
                 sm.lc[t][tid] = v;
@@ -412,6 +416,7 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
             // R in level order
             if (r < K && q < K)
                 sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
+            if (tid < K) sm.rinv[tid] = 1.0 / sm.rd[tid];
             __syncthreads();
             // U = R^-1 by rows from the bottom: U_i. = (e_i - sum_{m>i} R_im U_m.) / R_ii
             if (r < K && q < K) sm.lc[r][q] = make_double2(0.0, 0.0);
@@ -420,9 +425,9 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
                 if (tid < K) {
                     const int k = tid;
                     const double2 acc = sm.lc[m][k];
-                    const double rmm = sm.r[m][m].x;
+                    const double ri = sm.rinv[m];
                     sm.u[m][k] = (k < m) ? make_double2(0.0, 0.0)
-                                         : make_double2(((k == m ? 1.0 : 0.0) - acc.x) / rmm, -acc.y / rmm);
+                                         : make_double2(((k == m ? 1.0 : 0.0) - acc.x) * ri, -acc.y * ri);
                 }
                 __syncthreads();
                 if (r < m && q < K && q >= m) sm.lc[r][q] = zfma(sm.r[r][m], sm.u[m][q], sm.lc[r][q]);
@@ -450,12 +455,14 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
                 sm.u2[r][q] = v;
             }
             __syncthreads();
-            // A = U2^H U2 (Hermitian), into s
+            // A = U2^H U2 (Hermitian), as an FP32 hi + lo pair
             if (r < K && q < K) {
                 double2 v = make_double2(0.0, 0.0);
                 const int mx = r < q ? r : q;
                 for (int m = 0; m <= mx; ++m) v = zfma(zconj(sm.u2[m][r]), sm.u2[m][q], v);
-                sm.s[r][q] = v;
+                const float hx = (float)v.x, hy = (float)v.y;
+                sm.ahi[r][q] = make_float2(hx, hy);
+                sm.alo[r][q] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
             }
             __syncthreads();
             // outputs: row r of U~, w_r, user of level r
@@ -479,9 +486,8 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
                 float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
                 for (int j = 0; j < K; ++j) {
                     const float2 hv = sm.h[sm.uol[j]][m];
-                    const double2 av = sm.s[j][k];
-                    const float ahx = (float)av.x, ahy = (float)av.y;
-                    const float alx = (float)(av.x - (double)ahx), aly = (float)(av.y - (double)ahy);
+                    const float ahx = sm.ahi[j][k].x, ahy = sm.ahi[j][k].y;
+                    const float alx = sm.alo[j][k].x, aly = sm.alo[j][k].y;
                     // conj(h) * a = (h.x a.x + h.y a.y) + i (h.x a.y - h.y a.x)
                     dot2_acc(hv.x, ahx, re, ree);
                     dot2_acc(hv.y, ahy, re, ree);

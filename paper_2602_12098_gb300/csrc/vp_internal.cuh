@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/vp.h"
+#include "vp.h"
 
 namespace vp {
 

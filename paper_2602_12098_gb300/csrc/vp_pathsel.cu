@@ -14,7 +14,8 @@
 // from three doubling merges and one more (S+{0,1} -> S+{0..3} -> S+{0..7},
 // then with S+8), each cut to n entries: the n smallest of a union only need
 // the n smallest of each part. A merge is skipped when the shifted copy
-// starts after the current n-th entry. Each merge is a merge-path pass.
+// starts after the current n-th entry. Each merge is a merge-path pass of
+// one warp (8 outputs per lane at n = 256), synchronised with __syncwarp.
 #include "vp_internal.cuh"
 
 namespace vp {
@@ -26,6 +27,11 @@ struct PathArgs {
     int C, K, n, nch;
     DeviceState d;
 };
+
+// Shared-memory lists use a skewed index (one pad word per 8 entries): the
+// lanes of a merge own contiguous output ranges, and without the pad their
+// 64-bit accesses would fall on two banks only.
+__device__ __forceinline__ int sk(int i) { return i + (i >> 3); }
 
 __device__ __forceinline__ bool key_less(uint64_t am, uint64_t ac, uint64_t bm, uint64_t bc)
 {
@@ -46,44 +52,50 @@ __device__ void merge_shift(const uint64_t* Am, const uint64_t* Ac, int na,
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         const int bj = d0 - mid - 1;
-        if (key_less(Am[mid], Ac[mid], Bm[bj] + dm, Bc[bj] + dc)) lo = mid + 1;
+        if (key_less(Am[sk(mid)], Ac[sk(mid)], Bm[sk(bj)] + dm, Bc[sk(bj)] + dc)) lo = mid + 1;
         else hi = mid;
     }
     int i = lo, j = d0 - lo;
     for (int d = d0; d < d1; ++d) {
-        const bool takeA = (j >= nb) || (i < na && key_less(Am[i], Ac[i], Bm[j] + dm, Bc[j] + dc));
-        if (takeA) { Om[d] = Am[i]; Oc[d] = Ac[i]; ++i; }
-        else { Om[d] = Bm[j] + dm; Oc[d] = Bc[j] + dc; ++j; }
+        const bool takeA = (j >= nb) || (i < na && key_less(Am[sk(i)], Ac[sk(i)], Bm[sk(j)] + dm, Bc[sk(j)] + dc));
+        if (takeA) { Om[sk(d)] = Am[sk(i)]; Oc[sk(d)] = Ac[sk(i)]; ++i; }
+        else { Om[sk(d)] = Bm[sk(j)] + dm; Oc[sk(d)] = Bc[sk(j)] + dc; ++j; }
     }
 }
 
-__global__ void pathsel_kernel(PathArgs a)
+// One warp per channel; a block holds `cpb` channels (shared memory 48 n bytes each).
+__global__ void pathsel_kernel(PathArgs a, int cpb)
 {
     extern __shared__ uint64_t shm[];
-    __shared__ uint64_t qw[kMaxK];
-    const int n = a.n, K = a.K, T = blockDim.x, tid = threadIdx.x;
-    uint64_t* bm[3] = {shm, shm + 2 * n, shm + 4 * n};       // metrics of the three buffers
-    uint64_t* bc[3] = {shm + n, shm + 3 * n, shm + 5 * n};   // codes
-    const int c = blockIdx.x;
+    __shared__ uint64_t qws[8][kMaxK];
+    const int n = a.n, K = a.K;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * cpb + warp;
+    if (c >= a.C) return;
+    const int ns = sk(n);                                        // skewed length of one list
+    uint64_t* base = shm + (size_t)warp * 6 * ns;
+    uint64_t* bm[3] = {base, base + 2 * ns, base + 4 * ns};     // metrics of the three buffers
+    uint64_t* bc[3] = {base + ns, base + 3 * ns, base + 5 * ns}; // codes
+    uint64_t* qw = qws[warp];
     uint64_t* out = a.d.paths + (size_t)c * n;
     uint64_t* mqo = a.d.maxq + (size_t)c * a.nch;
 
     if (a.d.st[c] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
-        for (int i = tid; i < n; i += T) out[i] = 0;
-        for (int i = tid; i < a.nch; i += T) mqo[i] = 0;
+        for (int i = lane; i < n; i += 32) out[i] = 0;
+        for (int i = lane; i < a.nch; i += 32) mqo[i] = 0;
         return;
     }
-    if (tid == 0) {
-        float wmax = 0.f;
-        for (int l = 0; l < K; ++l) wmax = fmaxf(wmax, a.d.w[(size_t)c * K + l]);
+    {
+        const float wl = lane < K ? a.d.w[(size_t)c * K + lane] : 0.f;
+        float wmax = wl;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(kFull, wmax, o));
         int e;
         frexpf(wmax, &e);                      // wmax < 2^e, so 8 K w 2^(55-e) < 2^62
-        for (int l = 0; l < K; ++l)
-            qw[l] = __double2ull_rn(ldexp((double)a.d.w[(size_t)c * K + l], 55 - e));
-        bm[0][0] = 0;
-        bc[0][0] = 0;
+        if (lane < K) qw[lane] = __double2ull_rn(ldexp((double)wl, 55 - e));
+        if (lane == 0) { bm[0][0] = 0; bc[0][0] = 0; }
     }
-    __syncthreads();
+    __syncwarp(kFull);
 
     int iS = 0, s = 1;
     for (int l = 0; l < K; ++l) {
@@ -96,12 +108,12 @@ __global__ void pathsel_kernel(PathArgs a)
             const int ib = step < 3 ? ix : iS;
             const int nb = step < 3 ? nx : s;
             const uint64_t dm = mul * q, dc = mul * d1;
-            const bool skip = nx >= n && key_less(bm[ix][n - 1], bc[ix][n - 1], bm[ib][0] + dm, bc[ib][0] + dc);
+            const bool skip = nx >= n && key_less(bm[ix][sk(n - 1)], bc[ix][sk(n - 1)], bm[ib][0] + dm, bc[ib][0] + dc);
             if (skip) continue;
             const int io = (ix == iS) ? (iS + 1) % 3 : 3 - ix - iS;
             const int nout = min(nx + nb, n);
-            merge_shift(bm[ix], bc[ix], nx, bm[ib], bc[ib], nb, dm, dc, bm[io], bc[io], nout, tid, T);
-            __syncthreads();
+            merge_shift(bm[ix], bc[ix], nx, bm[ib], bc[ib], nb, dm, dc, bm[io], bc[io], nout, lane, 32);
+            __syncwarp(kFull);
             ix = io;
             nx = nout;
         }
@@ -110,11 +122,10 @@ __global__ void pathsel_kernel(PathArgs a)
     }
 
     const uint64_t* Sc = bc[iS];
-    for (int i = tid; i < n; i += T) out[i] = (i < s) ? Sc[i] : 0;
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int ch = warp; ch < a.nch; ch += T >> 5) {
+    for (int i = lane; i < n; i += 32) out[i] = (i < s) ? Sc[sk(i)] : 0;
+    for (int ch = 0; ch < a.nch; ++ch) {
         const int i = ch * 32 + lane;
-        const uint64_t code = (i < s) ? Sc[i] : 0;
+        const uint64_t code = (i < s) ? Sc[sk(i)] : 0;
         uint64_t mq = 0;
         for (int l = 0; l < K; ++l) {
             const unsigned dgt = (unsigned)((code >> (4 * l)) & 15u);
@@ -134,7 +145,11 @@ cudaError_t launch_pathsel(const vp_plan* p, int C, cudaStream_t s)
     a.n = p->n_paths;
     a.nch = n_chunks(p->n_paths);
     a.d = p->d;
-    const size_t shbytes = (size_t)6 * p->n_paths * sizeof(uint64_t);
+    const int ns = p->n_paths + (p->n_paths >> 3);
+    const size_t per = (size_t)6 * ns * sizeof(uint64_t);
+    int cpb = (int)((48 * 1024) / per);
+    cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
+    const size_t shbytes = per * cpb;
     static size_t attr_set = 0;
     if (shbytes > 40 * 1024 && shbytes > attr_set) {
         cudaError_t e = cudaFuncSetAttribute(pathsel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -142,10 +157,7 @@ cudaError_t launch_pathsel(const vp_plan* p, int C, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = shbytes;
     }
-    int T = 32;
-    if (p->n_paths > 64) T = 128;
-    if (p->n_paths > 256) T = 256;
-    pathsel_kernel<<<C, T, shbytes, s>>>(a);
+    pathsel_kernel<<<(C + cpb - 1) / cpb, 32 * cpb, shbytes, s>>>(a, cpb);
     return cudaGetLastError();
 }
 

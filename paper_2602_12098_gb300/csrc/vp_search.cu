@@ -34,90 +34,80 @@ struct SearchArgs {
     DeviceState d;
 };
 
-// DEMAP selection. Per axis the points of {-1,0,1} ordered by distance to
-// the coordinate c (ties to the smaller point) are n0, n1, n2 = -sg, with
-// n0 the rounding of c, sg = +1 for c > 0 else -1, n1 = sg if n0 = 0 else 0;
-// relative to n0 their squared distances grow by D1 = |1 - 2|c||
-// and D2 = max(1 + 2|c|, 4|c|). The 9 points form a 3x3 table of sums
-// Dx_i + Dy_j with sorted rows and columns (cell (i, j) = point (x_i, y_j)),
-// so the next nearest point is always a corner of the cells taken so far.
-// Exact ties go to the smaller alphabet index 3(tr+1) + (ti+1), i.e. to the
-// lexicographically smaller (tr, ti).
-struct Axis {
-    int n0, n1, n2;
-    float D1, D2;
-};
+// DEMAP selection: the q-th (0-based) nearest point t of {-1,0,1}+j{-1,0,1}
+// to the effective point c = (x, y), ties to the smaller alphabet index
+// 3(tr+1) + (ti+1), i.e. to the lexicographically smaller (tr, ti).
+//
+// Ties. Measuring from c - (eps_x, eps_y) with eps_x >> eps_y > 0 tiny orders
+// equal-distance points exactly by (tr, ti), so every comparison below is a
+// plain '<' on the shifted point. Exact ties only occur for dyadic centres
+// (|x|, |y| < 1/2, e.g. s/tau at the first level), where 2^-23 and 2^-25 are
+// representable shifts far below the spacing of distinct distances.
+//
+// Per axis (region r = [x > -1/2] + [x > 0] + [x > 1/2]) the points in
+// increasing distance are n_0, n_1, n_2 (kNTab), and their squared distances
+// exceed that of n_0 by 0, D1 = |1 - 2|x||, D2 = max(1 + 2|x|, 4|x|). The 9
+// points form a 3x3 table of sums Dx_i + Dy_j (cell (i, j) = (n_i(x), n_j(y))).
+// Against the origin cell the 8 others are
+//   A=(1,0): D1x  B=(0,1): D1y  C=(2,0): D2x  D=(0,2): D2y  E=(1,1): D1x+D1y
+//   F=(1,2): D1x+D2y  G=(2,1): D2x+D1y  H=(2,2): largest,
+// and every pair not ordered by the table's structure is one of
+//   f0 A<B, f1 C<B, f2 A<D, f3 C<D, f4 E<C, f5 E<D, f6 F<C, f7 G<D, f8 F<G,
+// so the rank of each cell is a short sum of these bits.
+constexpr float kEpsX = 0x1p-23f;
+constexpr float kEpsY = 0x1p-25f;
+// (n_i(r) + 1) in 2 bits at bit 2(3r + i): r0 (-1,0,1), r1 (0,-1,1), r2 (0,1,-1), r3 (1,0,-1)
+constexpr uint32_t kNTab = 0x189864u;
 
-__device__ __forceinline__ int round3(float c) { return (c > 0.5f) - (c <= -0.5f); }
+__device__ __forceinline__ int region4(float x) { return (x > -0.5f) + (x > 0.f) + (x > 0.5f); }
+__device__ __forceinline__ int npt(int r, int i) { return (int)((kNTab >> (2 * (3 * r + i))) & 3u) - 1; }
+__device__ __forceinline__ float gap1(float x) { return fabsf(fmaf(-2.f, fabsf(x), 1.f)); }
+__device__ __forceinline__ float gap2(float x) { return fmaxf(fmaf(2.f, fabsf(x), 1.f), 4.f * fabsf(x)); }
 
-__device__ __forceinline__ Axis axis_order(float c)
+// cell (ci, cj) of 0-based rank q >= 1 from the nine comparisons
+__device__ __forceinline__ void rank_cell(float D1x, float D2x, float D1y, float D2y, int q, int& ci, int& cj)
 {
-    Axis a;
-    a.n0 = round3(c);
-    const int sg = (c > 0.f) ? 1 : -1;
-    a.n1 = (a.n0 == 0) ? sg : 0;
-    a.n2 = -sg;
-    const float m = fabsf(c);
-    a.D1 = fabsf(fmaf(-2.f, m, 1.f));
-    a.D2 = fmaxf(fmaf(2.f, m, 1.f), 4.f * m);
-    return a;
+    const float vE = D1x + D1y, vF = D1x + D2y, vG = D2x + D1y;
+    const int f0 = D1x < D1y, f1 = D2x < D1y, f2 = D1x < D2y, f3 = D2x < D2y, f4 = vE < D2x;
+    const int f5 = vE < D2y, f6 = vF < D2x, f7 = vG < D2y, f8 = vF < vG;
+    const int k = q - 1;
+    const int rA = 2 - f0 - f2, rB = f0 + f1, rC = 3 - f1 - f3 + f4 + f6, rD = 1 + f2 + f3 + f5 + f7;
+    const int rE = 4 - f4 - f5, rF = 6 - f6 - f8, rG = 5 - f7 + f8;
+    ci = 2; cj = 2;                                                   // H
+    if (rG == k) { ci = 2; cj = 1; }
+    if (rF == k) { ci = 1; cj = 2; }
+    if (rE == k) { ci = 1; cj = 1; }
+    if (rD == k) { ci = 0; cj = 2; }
+    if (rC == k) { ci = 2; cj = 0; }
+    if (rB == k) { ci = 0; cj = 1; }
+    if (rA == k) { ci = 1; cj = 0; }
 }
 
-__device__ __forceinline__ int pick3(int j, int a0, int a1, int a2) { return j == 0 ? a0 : (j == 1 ? a1 : a2); }
-__device__ __forceinline__ float pick3f(int j, float a0, float a1, float a2) { return j == 0 ? a0 : (j == 1 ? a1 : a2); }
-
-// q in {0, 1, 2}: rank 1 is (n1x, n0y) or (n0x, n1y); rank 2 is the other one
-// or the next point along the axis already used.
-__device__ __forceinline__ void select_q2(float cx, float cy, int q, int& tr, int& ti)
+// t for rank q at effective point (cx, cy); `mq` = the warp's largest q at this
+// level (uniform) picks the cheapest branch that is exact for every lane.
+__device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, int& tr, int& ti)
 {
-    const Axis ax = axis_order(cx), ay = axis_order(cy);
-    // lexicographic tie-breaks: the two candidates differ in Re t, so compare it
-    const bool aFirst = ax.D1 < ay.D1 || (ax.D1 == ay.D1 && ax.n1 < ax.n0);
-    const bool oFirst = aFirst ? (ay.D1 < ax.D2 || (ay.D1 == ax.D2 && ax.n0 < ax.n2))
-                               : (ax.D1 < ay.D2 || (ax.D1 == ay.D2 && ax.n1 < ax.n0));
-    int ci = 0, cj = 0;
-    if (q == 1) {
-        ci = aFirst ? 1 : 0;
-        cj = aFirst ? 0 : 1;
-    } else if (q == 2) {
-        ci = aFirst ? (oFirst ? 0 : 2) : (oFirst ? 1 : 0);
-        cj = aFirst ? (oFirst ? 1 : 0) : (oFirst ? 0 : 2);
+    const float px = cx - kEpsX, py = cy - kEpsY;
+    if (mq == 0) {
+        tr = (px > 0.5f) - (px <= -0.5f);
+        ti = (py > 0.5f) - (py <= -0.5f);
+        return;
     }
-    tr = pick3(ci, ax.n0, ax.n1, ax.n2);
-    ti = pick3(cj, ay.n0, ay.n1, ay.n2);
-}
-
-// any q: walk the corners of the taken cells `mq` times (mq uniform, >= q)
-__device__ __noinline__ void select_general(float cx, float cy, int q, int mq, int& tr, int& ti)
-{
-    const Axis ax = axis_order(cx), ay = axis_order(cy);
-    int c0 = 1, c1 = 0, c2 = 0;   // cells taken in rows 0, 1, 2 ((0,0) is rank 0)
-    int ri = 0, rj = 0;
-    for (int step = 1; step <= mq; ++step) {
-        float bv = INFINITY;
-        int bidx = 99, brow = 0, bcol = 0;
-        if (c0 < 3) {
-            const float v = pick3f(c0, 0.f, ay.D1, ay.D2);
-            const int id = 3 * (ax.n0 + 1) + (pick3(c0, ay.n0, ay.n1, ay.n2) + 1);
-            if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 0; bcol = c0; }
-        }
-        if (c1 < c0) {
-            const float v = ax.D1 + pick3f(c1, 0.f, ay.D1, ay.D2);
-            const int id = 3 * (ax.n1 + 1) + (pick3(c1, ay.n0, ay.n1, ay.n2) + 1);
-            if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 1; bcol = c1; }
-        }
-        if (c2 < c1) {
-            const float v = ax.D2 + pick3f(c2, 0.f, ay.D1, ay.D2);
-            const int id = 3 * (ax.n2 + 1) + (pick3(c2, ay.n0, ay.n1, ay.n2) + 1);
-            if (v < bv || (v == bv && id < bidx)) { bv = v; bidx = id; brow = 2; bcol = c2; }
-        }
-        if (step <= q) { ri = brow; rj = bcol; }
-        c0 += (brow == 0);
-        c1 += (brow == 1);
-        c2 += (brow == 2);
+    const float D1x = gap1(px), D2x = gap2(px), D1y = gap1(py), D2y = gap2(py);
+    int ci, cj;
+    if (mq <= 2) {
+        const bool f0 = D1x < D1y;                                    // rank 1: A or B
+        const bool g = f0 ? (D1y < D2x) : (D1x < D2y);                // rank 2: the other, or C / D
+        const int c2i = f0 ? (g ? 0 : 2) : (g ? 1 : 0);
+        const int c2j = f0 ? (g ? 1 : 0) : (g ? 0 : 2);
+        ci = q == 0 ? 0 : (q == 1 ? (f0 ? 1 : 0) : c2i);
+        cj = q == 0 ? 0 : (q == 1 ? (f0 ? 0 : 1) : c2j);
+    } else {
+        rank_cell(D1x, D2x, D1y, D2y, q, ci, cj);
+        if (q == 0) { ci = 0; cj = 0; }
     }
-    tr = pick3(ri, ax.n0, ax.n1, ax.n2);
-    ti = pick3(rj, ay.n0, ay.n1, ay.n2);
+    tr = npt(region4(px), ci);
+    ti = npt(region4(py), cj);
 }
 
 template <int KT>
@@ -219,14 +209,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
                     const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
                     const float cx = r[lv].x, cy = r[lv].y;
                     int tr, ti;
-                    if (mql == 0) {
-                        tr = round3(cx);
-                        ti = round3(cy);
-                    } else if (mql <= 2) {
-                        select_q2(cx, cy, q, tr, ti);
-                    } else {
-                        select_general(cx, cy, q, mql, tr, ti);
-                    }
+                    select_point(cx, cy, q, mql, tr, ti);
                     const float ftr = (float)tr, fti = (float)ti;
                     const float dx = cx - ftr, dy = cy - fti;
                     ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
