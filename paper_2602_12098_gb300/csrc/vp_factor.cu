@@ -309,49 +309,70 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 }
 
 // ---------------------------------------------------------------------------
-// FP64 path for the flagged channels: one 256-thread block per channel,
-// thread (r, q) <-> matrix entry (r, q). GB300's FP64 rate is low, so FP64 is
-// kept to the pivoted Cholesky of the Gram matrix, U = R^-1 and one Newton
-// step; the Gram matrix and P are accumulated in compensated FP32 (exact
-// products of the FP32 inputs, ~48-bit sums).
+// FP64 path for the flagged channels: one warp per channel, lanes strided over
+// the entries of each (triangular) matrix operation. GB300 issues FP64 FMAs
+// at 1/64 of the FP32 rate, so FP64 is kept to the pivoted Cholesky of the
+// Gram matrix, U = R^-1 and one Newton step, with the lanes of every FP64
+// instruction packed; the Gram matrix, A = U2^H U2 and P = H^H A are
+// accumulated in compensated FP32 (exact products, ~48-bit sums).
+
+constexpr int kW64 = 1;   // channels (warps) per block (27 KB of shared memory each)
 
 struct Smem64 {
     float2 h[kMaxK][kMaxM];      // H rows (user order)
-    double2 s[kMaxK][kMaxK];     // Gram / Schur complement, lower triangle (user index); later A = U2^H U2
-    double2 lc[kMaxK][kMaxK];    // lc[t][j]: column of R at level t, by user j; later the substitution sums
-    double2 r[kMaxK][kMaxK];     // R, level order; later E = I - R U
-    double2 u[kMaxK][kMaxK];     // U = R^-1
-    double2 u2[kMaxK][kMaxK];    // U after one Newton step
-    float2 ahi[kMaxK][kMaxK];    // A = U2^H U2 split into FP32 hi + lo
+    double2 s[kMaxK][kMaxK];     // Gram / Schur complement (both triangles, user index); later E
+    double2 lc[kMaxK][kMaxK];    // lc[t][u]: column of R at level t, by user; later substitution sums
+    double2 r[kMaxK][kMaxK];     // R, level order
+    double2 u[kMaxK][kMaxK];     // U = R^-1, then U2 after the Newton step
+    float2 uh[kMaxK][kMaxK];     // U2 as FP32 hi + lo
+    float2 ul[kMaxK][kMaxK];
+    float2 ahi[kMaxK][kMaxK];    // A = U2^H U2 as FP32 hi + lo
     float2 alo[kMaxK][kMaxK];
-    double2 pc[kMaxK];           // pivot column / R_tt of the current step
+    double2 pc[kMaxK];           // pivot column of the current step (by remaining position)
     double rd[kMaxK];
-    double rinv[kMaxK];          // 1 / R_mm
+    double rinv[kMaxK];
     int uol[kMaxK];
-    double dmax;
-    double pivv;
-    int piv;
+    int rem[kMaxK];              // remaining users
 };
 
-__device__ __forceinline__ double2 s_at(const Smem64& sm, int i, int j)   // Schur entry (i, j) from the lower triangle
+// e-th entry (e < n(n+1)/2) of a lower triangle: a >= b
+__device__ __forceinline__ void tri_index(int e, int& a, int& b)
 {
-    return i >= j ? sm.s[i][j] : zconj(sm.s[j][i]);
+    int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    while (r * (r + 1) / 2 > e) --r;
+    a = r;
+    b = e - r * (r + 1) / 2;
 }
 
-__global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
+// (hi, lo) += x * y for a complex FP32 pair y = yh + yl (x exact FP32)
+__device__ __forceinline__ void cdot2(float2 x, float2 yh, float2 yl, float& re, float& ree, float& im, float& ime)
 {
-    __shared__ Smem64 sm;
-    const int tid = threadIdx.x;
-    const int r = tid >> 4, q = tid & 15;
+    dot2_acc(x.x, yh.x, re, ree);
+    dot2_acc(-x.y, yh.y, re, ree);
+    dot2_acc(x.x, yh.y, im, ime);
+    dot2_acc(x.y, yh.x, im, ime);
+    ree = fmaf(x.x, yl.x, fmaf(-x.y, yl.y, ree));
+    ime = fmaf(x.x, yl.y, fmaf(x.y, yl.x, ime));
+}
+
+__global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
+{
+    __shared__ Smem64 smem[kW64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Smem64& sm = smem[warp];
     const int K = a.K, M = a.M;
     const int nflag = *a.d.nflag;
 
-    for (int slot = blockIdx.x; slot < nflag; slot += gridDim.x) {
+    for (int slot = blockIdx.x * kW64 + warp; slot < nflag; slot += gridDim.x * kW64) {
         const int c = a.d.flags[slot];
-        for (int i = tid; i < K * M; i += blockDim.x) sm.h[i / M][i % M] = a.H[(size_t)c * K * M + i];
-        __syncthreads();
-        // Gram, lower triangle: G_rq = sum_m h_rm conj(h_qm), compensated FP32 -> FP64
-        if (r < K && q <= r) {
+        for (int i = lane; i < K * M; i += 32) sm.h[i / M][i % M] = a.H[(size_t)c * K * M + i];
+        if (lane < K) sm.rem[lane] = lane;
+        __syncwarp();
+        // Gram matrix (compensated FP32, exact for FP32 input), both triangles in FP64
+        for (int e = lane; e < K * (K + 1) / 2; e += 32) {
+            int r, q;
+            tri_index(e, r, q);
             float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
             for (int m = 0; m < M; ++m) {
                 const float2 x = sm.h[r][m], y = sm.h[q][m];
@@ -360,141 +381,158 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
                 dot2_acc(x.y, y.x, im, ime);
                 dot2_acc(-x.x, y.y, im, ime);
             }
-            sm.s[r][q] = make_double2((double)re + (double)ree, (double)im + (double)ime);
+            const double2 g = make_double2((double)re + (double)ree, (double)im + (double)ime);
+            sm.s[r][q] = g;
+            sm.s[q][r] = zconj(g);
         }
-        __syncthreads();
-        if (tid == 0) {
-            double dm = 0.0;
-            for (int j = 0; j < K; ++j) dm = fmax(dm, sm.s[j][j].x);
-            sm.dmax = dm;
-        }
-
-        // pivoted reverse Cholesky: at level t (from K-1 down) the remaining user
-        // with the smallest Schur diagonal (ties: lowest user) becomes the pivot
-        unsigned remm = (1u << K) - 1u;
-        bool singular = false;
-        for (int t = K - 1; t >= 0 && !singular; --t) {
-            __syncthreads();
-            if (tid < 32) {
-                double key = (tid < K && ((remm >> tid) & 1u)) ? sm.s[tid][tid].x : INFINITY;
-                int kj = tid;
+        __syncwarp();
+        double dmax = lane < K ? sm.s[lane][lane].x : 0.0;
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) {
-                    const double ok = __shfl_xor_sync(kFull, key, off);
-                    const int oj = __shfl_xor_sync(kFull, kj, off);
-                    if (ok < key || (ok == key && oj < kj)) { key = ok; kj = oj; }
-                }
-                if (tid == 0) { sm.piv = kj; sm.pivv = key; }
+        for (int o = 16; o >= 1; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+
+        // pivoted reverse Cholesky (level t from K-1 down: smallest Schur diagonal, ties to the lowest user)
+        bool singular = false;
+        for (int t = K - 1; t >= 0; --t) {
+            const int m = t + 1;                                       // remaining users before the pivot
+            double key = INFINITY;
+            int ku = 0x7fffffff, kp = lane;
+            if (lane < m) { ku = sm.rem[lane]; key = sm.s[ku][ku].x; }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const double ok = __shfl_xor_sync(kFull, key, o);
+                const int ou = __shfl_xor_sync(kFull, ku, o), op = __shfl_xor_sync(kFull, kp, o);
+                if (ok < key || (ok == key && ou < ku)) { key = ok; ku = ou; kp = op; }
             }
-            __syncthreads();
-            const int p = sm.piv;
-            const double pv = sm.pivv;
-            if (!(pv > 1e-12 * sm.dmax)) { singular = true; break; }   // uniform: every thread reads the same values
-            const double rt = sqrt(pv);
-            const double irt = 1.0 / rt;
-            remm &= ~(1u << p);
-            if (tid < K) {
-                double2 v = make_double2(0.0, 0.0);
-                if ((remm >> tid) & 1u) {
-                    const double2 sp = s_at(sm, tid, p);
-                    v = make_double2(sp.x * irt, sp.y * irt);
-                }
-                sm.pc[tid] = v;
-                sm.lc[t][tid] = v;
+            if (!(key > 1e-12 * dmax)) { singular = true; break; }      // uniform across the warp
+            const int p = ku;
+            const double rt = sqrt(key), irt = 1.0 / rt;
+            // remove p from the remaining list (move the last one into its position)
+            const int last = sm.rem[m - 1];
+            __syncwarp();
+            if (lane == 0) {
+                sm.rem[kp] = last;
+                sm.rd[t] = rt;
+                sm.uol[t] = p;
             }
-            if (tid == 0) { sm.rd[t] = rt; sm.uol[t] = p; }
-            __syncthreads();
-            if (r < K && q <= r && ((remm >> r) & 1u) && ((remm >> q) & 1u)) {
-                const double2 pr = zmul(sm.pc[r], zconj(sm.pc[q]));
-                sm.s[r][q].x -= pr.x;
-                sm.s[r][q].y -= pr.y;
+            __syncwarp();
+            if (lane < m - 1) {
+                const double2 v = sm.s[sm.rem[lane]][p];
+                const double2 l = make_double2(v.x * irt, v.y * irt);
+                sm.pc[lane] = l;
+                sm.lc[t][sm.rem[lane]] = l;
             }
+            __syncwarp();
+            for (int e = lane; e < (m - 1) * m / 2; e += 32) {        // Schur update, packed lower triangle
+                int ia, ib;
+                tri_index(e, ia, ib);
+                const int ua = sm.rem[ia], ub = sm.rem[ib];
+                const double2 pr = zmul(sm.pc[ia], zconj(sm.pc[ib]));
+                const double2 v = make_double2(sm.s[ua][ub].x - pr.x, sm.s[ua][ub].y - pr.y);
+                sm.s[ua][ub] = v;
+                sm.s[ub][ua] = zconj(v);
+            }
+            __syncwarp();
         }
-        __syncthreads();
 
         if (!singular) {
-            // R in level order
-            if (r < K && q < K)
+            for (int e = lane; e < K * K; e += 32) {                    // R in level order
+                const int r = e / K, q = e % K;
                 sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
-            if (tid < K) sm.rinv[tid] = 1.0 / sm.rd[tid];
-            __syncthreads();
-            // U = R^-1 by rows from the bottom: U_i. = (e_i - sum_{m>i} R_im U_m.) / R_ii
-            if (r < K && q < K) sm.lc[r][q] = make_double2(0.0, 0.0);
-            __syncthreads();
+            }
+            if (lane < K) sm.rinv[lane] = 1.0 / sm.rd[lane];
+            __syncwarp();
+            for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = make_double2(0.0, 0.0);
+            __syncwarp();
+            // U = R^-1 by rows from the bottom: U_m. = (e_m - sum_{j>m} R_mj U_j.) / R_mm
             for (int m = K - 1; m >= 0; --m) {
-                if (tid < K) {
-                    const int k = tid;
+                if (lane < K) {
+                    const int k = lane;
                     const double2 acc = sm.lc[m][k];
                     const double ri = sm.rinv[m];
                     sm.u[m][k] = (k < m) ? make_double2(0.0, 0.0)
                                          : make_double2(((k == m ? 1.0 : 0.0) - acc.x) * ri, -acc.y * ri);
                 }
-                __syncthreads();
-                if (r < m && q < K && q >= m) sm.lc[r][q] = zfma(sm.r[r][m], sm.u[m][q], sm.lc[r][q]);
-                __syncthreads();
-            }
-            // one Newton step: E = I - R U, U2 = U + U E (upper triangular)
-            double2 e = make_double2(0.0, 0.0);
-            if (r < K && q < K && q >= r) {
-                e = make_double2(r == q ? 1.0 : 0.0, 0.0);
-                for (int m = r; m <= q; ++m) {
-                    const double2 pr = zmul(sm.r[r][m], sm.u[m][q]);
-                    e.x -= pr.x;
-                    e.y -= pr.y;
+                __syncwarp();
+                const int w = K - m;                                    // entries (i < m, k >= m)
+                for (int e = lane; e < m * w; e += 32) {
+                    const int i = e / w, k = m + e % w;
+                    sm.lc[i][k] = zfma(sm.r[i][m], sm.u[m][k], sm.lc[i][k]);
                 }
+                __syncwarp();
             }
-            __syncthreads();
-            if (r < K && q < K) sm.r[r][q] = e;
-            __syncthreads();
-            if (r < K && q < K) {
-                double2 v = make_double2(0.0, 0.0);
-                if (q >= r) {
-                    v = sm.u[r][q];
-                    for (int m = r; m <= q; ++m) v = zfma(sm.u[r][m], sm.r[m][q], v);
+            // one Newton step: E = I - R U, U2 = U + U E (both upper triangular), accumulated by rank-1 steps
+            for (int e = lane; e < K * K; e += 32) {
+                const int r = e / K, q = e % K;
+                sm.s[r][q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
+            }
+            __syncwarp();
+            for (int m = 0; m < K; ++m) {                               // E_ik -= R_im U_mk, i <= m <= k
+                const int w = K - m;
+                for (int e = lane; e < (m + 1) * w; e += 32) {
+                    const int i = e / w, k = m + e % w;
+                    const double2 pr = zmul(sm.r[i][m], sm.u[m][k]);
+                    sm.s[i][k].x -= pr.x;
+                    sm.s[i][k].y -= pr.y;
                 }
-                sm.u2[r][q] = v;
+                __syncwarp();
             }
-            __syncthreads();
-            // A = U2^H U2 (Hermitian), as an FP32 hi + lo pair
-            if (r < K && q < K) {
-                double2 v = make_double2(0.0, 0.0);
-                const int mx = r < q ? r : q;
-                for (int m = 0; m <= mx; ++m) v = zfma(zconj(sm.u2[m][r]), sm.u2[m][q], v);
+            for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = sm.u[e / K][e % K];
+            __syncwarp();
+            for (int m = 0; m < K; ++m) {                               // U2_ik += U_im E_mk, i <= m <= k
+                const int w = K - m;
+                for (int e = lane; e < (m + 1) * w; e += 32) {
+                    const int i = e / w, k = m + e % w;
+                    sm.lc[i][k] = zfma(sm.u[i][m], sm.s[m][k], sm.lc[i][k]);
+                }
+                __syncwarp();
+            }
+            // U2 (in lc) as FP32 hi + lo; outputs: row r of U~, w_r, user of level r
+            for (int e = lane; e < K * K; e += 32) {
+                const int r = e / K, q = e % K;
+                const double2 v = sm.lc[r][q];
                 const float hx = (float)v.x, hy = (float)v.y;
-                sm.ahi[r][q] = make_float2(hx, hy);
-                sm.alo[r][q] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
-            }
-            __syncthreads();
-            // outputs: row r of U~, w_r, user of level r
-            if (r < K && q < K) {
-                const double urr = sm.u2[r][r].x;
-                const double2 uv = sm.u2[r][q];
-                const float2 ut = (q > r) ? make_float2((float)(uv.x / urr), (float)(uv.y / urr))
+                sm.uh[r][q] = make_float2(hx, hy);
+                sm.ul[r][q] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+                const double urr = sm.lc[r][r].x;
+                const float2 ut = (q > r) ? make_float2((float)(v.x / urr), (float)(v.y / urr))
                                           : (q == r ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
                 a.d.utp[((size_t)c * K + r) * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
                 a.d.utc[((size_t)c * K + q) * K + r] = ut;
-                if (a.U_out) a.U_out[((size_t)c * K + r) * K + q] = make_float2((float)uv.x, (float)uv.y);
+                if (a.U_out) a.U_out[((size_t)c * K + r) * K + q] = make_float2(hx, hy);
                 if (q == 0) {
                     a.d.w[(size_t)c * K + r] = (float)(urr * urr);
                     a.d.ul[(size_t)c * K + r] = (uint8_t)sm.uol[r];
                     if (a.ul_out) a.ul_out[(size_t)c * K + r] = (uint8_t)sm.uol[r];
                 }
             }
-            // P_level[m][k] = sum_j conj(H_perm[j][m]) A[j][k], compensated FP32 with A = hi + lo
-            for (int e2 = tid; e2 < M * K; e2 += blockDim.x) {
-                const int m = e2 / K, k = e2 % K;
+            __syncwarp();
+            // A = U2^H U2 (Hermitian) in compensated FP32: A_ik = sum_{m <= min(i,k)} conj(U2_mi) U2_mk
+            for (int e = lane; e < K * (K + 1) / 2; e += 32) {
+                int i, k;
+                tri_index(e, i, k);                                     // i >= k
+                float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
+                for (int m = 0; m <= k; ++m) {
+                    const float2 xh = sm.uh[m][i], xl = sm.ul[m][i];
+                    const float2 cx = make_float2(xh.x, -xh.y);
+                    cdot2(cx, sm.uh[m][k], sm.ul[m][k], re, ree, im, ime);
+                    ree = fmaf(xl.x, sm.uh[m][k].x, fmaf(xl.y, sm.uh[m][k].y, ree));    // conj(xl) * yh
+                    ime = fmaf(xl.x, sm.uh[m][k].y, fmaf(-xl.y, sm.uh[m][k].x, ime));
+                }
+                const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
+                const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
+                sm.ahi[i][k] = hi;
+                sm.alo[i][k] = lo;
+                sm.ahi[k][i] = make_float2(hi.x, -hi.y);
+                sm.alo[k][i] = make_float2(lo.x, -lo.y);
+            }
+            __syncwarp();
+            // P_level[m][k] = sum_j conj(H_perm[j][m]) A[j][k], compensated FP32
+            for (int e = lane; e < M * K; e += 32) {
+                const int m = e / K, k = e % K;
                 float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
                 for (int j = 0; j < K; ++j) {
                     const float2 hv = sm.h[sm.uol[j]][m];
-                    const float ahx = sm.ahi[j][k].x, ahy = sm.ahi[j][k].y;
-                    const float alx = sm.alo[j][k].x, aly = sm.alo[j][k].y;
-                    // conj(h) * a = (h.x a.x + h.y a.y) + i (h.x a.y - h.y a.x)
-                    dot2_acc(hv.x, ahx, re, ree);
-                    dot2_acc(hv.y, ahy, re, ree);
-                    dot2_acc(hv.x, ahy, im, ime);
-                    dot2_acc(-hv.y, ahx, im, ime);
-                    ree = fmaf(hv.x, alx, fmaf(hv.y, aly, ree));
-                    ime = fmaf(hv.x, aly, fmaf(-hv.y, alx, ime));
+                    cdot2(make_float2(hv.x, -hv.y), sm.ahi[j][k], sm.alo[j][k], re, ree, im, ime);
                 }
                 const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
                 const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
@@ -503,12 +541,12 @@ __global__ void __launch_bounds__(256) factor64_kernel(FactorArgs a)
                 a.d.ptlo[((size_t)c * K + uk) * M + m] = lo;
                 if (a.P_out) a.P_out[((size_t)c * M + m) * K + uk] = hi;
             }
-            if (tid == 0) a.d.st[c] = (uint8_t)VP_CH_FP64;
+            if (lane == 0) a.d.st[c] = (uint8_t)VP_CH_FP64;
         } else {
-            if (tid < 16) write_channel_outputs_zero(a, c, tid);
-            if (tid == 0) a.d.st[c] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
+            if (lane < 16) write_channel_outputs_zero(a, c, lane);
+            if (lane == 0) a.d.st[c] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -545,8 +583,9 @@ cudaError_t launch_factor64(const vp_plan* p, const float2* H, int C, float2* U_
                             uint8_t* ul_out, cudaStream_t s)
 {
     const FactorArgs a = make_args(p, H, C, U_out, P_out, ul_out);
-    int blocks = C < 152 * 8 ? C : 152 * 8;
-    factor64_kernel<<<blocks, 256, 0, s>>>(a);
+    int blocks = (C + kW64 - 1) / kW64;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    factor64_kernel<<<blocks, 32 * kW64, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,9 @@
 // strict total order. With it K-Best keeps exactly the n smallest vectors,
 // whatever the level order.
 //
-// Level step: the children of the survivors S are S + k (q_l, 1 << 4l),
+// Levels are visited in increasing weight (K-Best is exact in any level
+// order under this total order), which lets fewer children enter the later
+// levels. Level step: the children of the survivors S are S + k (q_l, 1 << 4l),
 // k = 0..8, all shifted copies of the sorted list S. Their n smallest follow
 // from three doubling merges and one more (S+{0,1} -> S+{0..3} -> S+{0..7},
 // then with S+8), each cut to n entries: the n smallest of a union only need
@@ -39,27 +41,44 @@ __device__ __forceinline__ bool key_less(uint64_t am, uint64_t ac, uint64_t bm, 
 }
 
 // First `nout` outputs of the merge of sorted A[0..na) with the sorted list
-// B[0..nb) shifted by (dm, dc), into O. Threads split the output range.
+// B[0..nb) shifted by (dm, dc), into O; lane j writes outputs [j*per, (j+1)*per).
+// The metric decides; the code is compared only when two metrics are equal.
 __device__ void merge_shift(const uint64_t* Am, const uint64_t* Ac, int na,
                             const uint64_t* Bm, const uint64_t* Bc, int nb, uint64_t dm, uint64_t dc,
-                            uint64_t* Om, uint64_t* Oc, int nout, int tid, int T)
+                            uint64_t* Om, uint64_t* Oc, int nout, int lane)
 {
-    const int per = (nout + T - 1) / T;
-    const int d0 = min(tid * per, nout);
+    const int per = (nout + 31) >> 5;
+    const int d0 = min(lane * per, nout);
     const int d1 = min(d0 + per, nout);
     if (d0 >= d1) return;
     int lo = max(0, d0 - nb), hi = min(d0, na);
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         const int bj = d0 - mid - 1;
-        if (key_less(Am[sk(mid)], Ac[sk(mid)], Bm[sk(bj)] + dm, Bc[sk(bj)] + dc)) lo = mid + 1;
+        const uint64_t am = Am[sk(mid)], bmv = Bm[sk(bj)] + dm;
+        const bool lt = am < bmv || (am == bmv && Ac[sk(mid)] < Bc[sk(bj)] + dc);
+        if (lt) lo = mid + 1;
         else hi = mid;
     }
     int i = lo, j = d0 - lo;
+    uint64_t am = i < na ? Am[sk(i)] : ~0ull;
+    uint64_t bmv = j < nb ? Bm[sk(j)] + dm : ~0ull;
     for (int d = d0; d < d1; ++d) {
-        const bool takeA = (j >= nb) || (i < na && key_less(Am[sk(i)], Ac[sk(i)], Bm[sk(j)] + dm, Bc[sk(j)] + dc));
-        if (takeA) { Om[sk(d)] = Am[sk(i)]; Oc[sk(d)] = Ac[sk(i)]; ++i; }
-        else { Om[sk(d)] = Bm[sk(j)] + dm; Oc[sk(d)] = Bc[sk(j)] + dc; ++j; }
+        bool takeA;
+        if (j >= nb) takeA = true;
+        else if (i >= na) takeA = false;
+        else takeA = am < bmv || (am == bmv && Ac[sk(i)] < Bc[sk(j)] + dc);
+        if (takeA) {
+            Om[sk(d)] = am;
+            Oc[sk(d)] = Ac[sk(i)];
+            ++i;
+            am = i < na ? Am[sk(i)] : ~0ull;
+        } else {
+            Om[sk(d)] = bmv;
+            Oc[sk(d)] = Bc[sk(j)] + dc;
+            ++j;
+            bmv = j < nb ? Bm[sk(j)] + dm : ~0ull;
+        }
     }
 }
 
@@ -68,15 +87,19 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
 {
     extern __shared__ uint64_t shm[];
     __shared__ uint64_t qws[8][kMaxK];
+    __shared__ int ords[8][kMaxK];
     const int n = a.n, K = a.K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * cpb + warp;
     if (c >= a.C) return;
     const int ns = sk(n);                                        // skewed length of one list
     uint64_t* base = shm + (size_t)warp * 6 * ns;
-    uint64_t* bm[3] = {base, base + 2 * ns, base + 4 * ns};     // metrics of the three buffers
-    uint64_t* bc[3] = {base + ns, base + 3 * ns, base + 5 * ns}; // codes
+    // buffer b (0..2): metrics at base + 2 b ns, codes at base + (2 b + 1) ns
+    // (pointer arithmetic: an indexed pointer array would live in local memory)
+#define BM(b) (base + 2 * (b) * ns)
+#define BC(b) (base + (2 * (b) + 1) * ns)
     uint64_t* qw = qws[warp];
+    int* ord = ords[warp];
     uint64_t* out = a.d.paths + (size_t)c * n;
     uint64_t* mqo = a.d.maxq + (size_t)c * a.nch;
 
@@ -93,12 +116,22 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         int e;
         frexpf(wmax, &e);                      // wmax < 2^e, so 8 K w 2^(55-e) < 2^62
         if (lane < K) qw[lane] = __double2ull_rn(ldexp((double)wl, 55 - e));
-        if (lane == 0) { bm[0][0] = 0; bc[0][0] = 0; }
+        // levels in increasing weight (ties: lower level): fewer children enter the later levels
+        if (lane < K) {
+            int rank = 0;
+            for (int k = 0; k < K; ++k) {
+                const float wk = a.d.w[(size_t)c * K + k];
+                rank += (wk < wl) || (wk == wl && k < lane);
+            }
+            ord[rank] = lane;
+        }
+        if (lane == 0) { BM(0)[0] = 0; BC(0)[0] = 0; }
     }
     __syncwarp(kFull);
 
     int iS = 0, s = 1;
-    for (int l = 0; l < K; ++l) {
+    for (int li = 0; li < K; ++li) {
+        const int l = ord[li];
         const uint64_t q = qw[l];
         const uint64_t d1 = 1ull << (4 * l);
         int ix = iS, nx = s;
@@ -108,11 +141,11 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
             const int ib = step < 3 ? ix : iS;
             const int nb = step < 3 ? nx : s;
             const uint64_t dm = mul * q, dc = mul * d1;
-            const bool skip = nx >= n && key_less(bm[ix][sk(n - 1)], bc[ix][sk(n - 1)], bm[ib][0] + dm, bc[ib][0] + dc);
+            const bool skip = nx >= n && key_less(BM(ix)[sk(n - 1)], BC(ix)[sk(n - 1)], BM(ib)[0] + dm, BC(ib)[0] + dc);
             if (skip) continue;
             const int io = (ix == iS) ? (iS + 1) % 3 : 3 - ix - iS;
             const int nout = min(nx + nb, n);
-            merge_shift(bm[ix], bc[ix], nx, bm[ib], bc[ib], nb, dm, dc, bm[io], bc[io], nout, lane, 32);
+            merge_shift(BM(ix), BC(ix), nx, BM(ib), BC(ib), nb, dm, dc, BM(io), BC(io), nout, lane);
             __syncwarp(kFull);
             ix = io;
             nx = nout;
@@ -121,7 +154,9 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         s = nx;
     }
 
-    const uint64_t* Sc = bc[iS];
+    const uint64_t* Sc = BC(iS);
+#undef BM
+#undef BC
     for (int i = lane; i < n; i += 32) out[i] = (i < s) ? Sc[sk(i)] : 0;
     for (int ch = 0; ch < a.nch; ++ch) {
         const int i = ch * 32 + lane;

@@ -8,8 +8,7 @@
 // registers in units of tau (r' = r / tau is the effective point s_hat_l of
 // Eq. (17)); choosing t_l at level l updates them column-wise,
 //   r'_m -= U~_ml t_l,  m < l,
-// with two packed FP32 FMAs per complex term (skipped when every lane of the
-// warp chose t_l = 0), and t_l is the p_l-th nearest point of
+// with two packed FP32 FMAs per complex term, and t_l is the p_l-th nearest point of
 // {-1,0,1}+j{-1,0,1} to r'_l (DEMAP), ties to the smaller (Re t, Im t).
 // The PED grows by w_l tau^2 |r'_l - t_l|^2.
 // The zero perturbation is candidate 0; the warp's (PED, index) minimum wins
@@ -93,9 +92,16 @@ __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, 
         ti = (py > 0.5f) - (py <= -0.5f);
         return;
     }
+    if (mq == 1) {                                                    // rank 0 or 1: round, or step to A or B
+        const bool f0 = gap1(px) < gap1(py);
+        const int ci = (q == 1 && f0) ? 1 : 0, cj = (q == 1 && !f0) ? 1 : 0;
+        tr = npt(region4(px), ci);
+        ti = npt(region4(py), cj);
+        return;
+    }
     const float D1x = gap1(px), D2x = gap2(px), D1y = gap1(py), D2y = gap2(py);
     int ci, cj;
-    if (mq <= 2) {
+    if (mq == 2) {
         const bool f0 = D1x < D1y;                                    // rank 1: A or B
         const bool g = f0 ? (D1y < D2x) : (D1x < D2y);                // rank 2: the other, or C / D
         const int c2i = f0 ? (g ? 0 : 2) : (g ? 1 : 0);
@@ -111,7 +117,7 @@ __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, 
 }
 
 template <int KT>
-__global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
+__global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = a.K, M = a.M, n = a.n, nch = a.nch;
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a)
                     ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
                     const uint32_t dig = (uint32_t)((tr + 1) | ((ti + 1) << 2)) << sh;
                     if (lv < 8) lc0 |= dig; else lc1 |= dig;
-                    if (lv > 0 && (lv < 4 || __any_sync(kFull, (tr | ti) != 0))) {
+                    if (lv > 0) {
                         const float2 c1 = make_float2(-ftr, -ftr);
                         const float2 c2 = make_float2(fti, -fti);
 #pragma unroll
@@ -318,11 +324,12 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     a.tau = p->tau;
     a.inv_tau = 1.0f / p->tau;
     a.d = p->d;
-    // warps per block: a divisor-friendly count of the vectors per channel
+    // warps per block (<= 7, the register budget of 4 blocks per SM): a
+    // divisor-friendly count of the vectors per channel
     const int per = vec_off ? (n_vec + p->C - 1) / p->C : S;
-    int nw = 8;
-    if (per <= 8) nw = per < 1 ? 1 : per;
-    else if (per % 7 == 0) nw = 7;
+    int nw = 7;
+    if (per <= 7) nw = per < 1 ? 1 : per;
+    else if (per % 7 != 0 && per % 6 == 0) nw = 6;
     const int threads = nw * 32;
     const int K = p->K;
     if (K <= 2) return launch_kt<2>(a, p->C, threads, s);
