@@ -59,7 +59,8 @@ typedef enum {
     VP_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed */
     VP_ERR_OOM = 3,            /* device allocation failed */
     VP_ERR_TIMEOUT = 4,        /* a bounded device wait gave up */
-    VP_ERR_NOT_FACTORIZED = 5  /* vp_precode before vp_factorize, or for more channels */
+    VP_ERR_NOT_FACTORIZED = 5, /* vp_precode before vp_factorize, or for more channels */
+    VP_ERR_CAPACITY = 6        /* the request exceeds the fixed storage of vp_precode_noalloc */
 } vp_status;
 
 /* Per-channel status bits (the `status` output of vp_factorize). */
@@ -153,6 +154,35 @@ vp_status vp_get_paths(vp_plan* plan, uint64_t* codes, void* stream);
  */
 vp_status vp_run_slot_host(vp_plan* plan, const void* H_host, int C, const uint8_t* sym_host,
                            int S, void* x_host, int8_t* l_host, float* gamma_host, void* stream);
+
+/*
+ * One slot like vp_factorize + vp_precode (S symbols per channel), without
+ * allocating anything. The paper has no counterpart. It serves callers that
+ * cannot let a library call cudaMalloc: real-time slot loops, where
+ * cudaMalloc may synchronise the device and take unbounded time inside a
+ * slot's deadline; processes whose device memory is reserved up front by
+ * another framework's allocator; hosts that only hand this library device
+ * buffers. The per-channel state that a plan keeps
+ * in cudaMalloc'd memory lives instead in one static device array of
+ * vp_noalloc_capacity_bytes() bytes (8 MiB, e.g. 640 channels at K = M = 16
+ * with 256 paths); every GPU that loads the library holds that array until
+ * the process exits.
+ *   plan     supplies the parameters only (K, M, qam, n_paths, tau, FP64
+ *            threshold); its own device state is neither used nor allocated
+ *   H        complex64 [C][K][M]; sym_idx uint8 [C*S][K] (vector v -> channel v / S)
+ *   x, l, gamma  as vp_precode; status optional uint8 [C] as vp_factorize
+ * Returns VP_ERR_CAPACITY when C channels of this shape do not fit, with
+ * nothing enqueued. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls share the one array, which keeps
+ * the last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race on it, so serialise them.
+ */
+vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const uint8_t* sym_idx, int S,
+                             void* x, int8_t* l, float* gamma, uint8_t* status, void* stream);
+
+/* Size in bytes of the static device array behind vp_precode_noalloc. */
+size_t vp_noalloc_capacity_bytes(void);
 
 /* Number of kernel launches the last vp_factorize / vp_precode /
  * vp_run_slot_host call enqueued (copies and memsets not counted). */

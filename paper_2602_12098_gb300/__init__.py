@@ -23,7 +23,7 @@ __all__ = [
     "VPError", "load", "build", "library_path",
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize", "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
-    "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
     "EXPORTED_SYMBOLS", "Plan",
 ]
 
@@ -37,6 +37,7 @@ VP_MAX_PATHS = 1024
 EXPORTED_SYMBOLS = (
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize", "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes",
 )
 
 _lock = threading.Lock()
@@ -77,10 +78,13 @@ def load():
             L.vp_run_slot_host.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp]
             L.vp_last_launch_count.argtypes = [vpp]
             L.vp_last_launch_count.restype = ctypes.c_int
+            L.vp_precode_noalloc.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp, vpp]
+            L.vp_noalloc_capacity_bytes.argtypes = []
+            L.vp_noalloc_capacity_bytes.restype = ctypes.c_size_t
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
             for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize",
-                         "vp_precode", "vp_get_paths", "vp_run_slot_host"):
+                         "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_precode_noalloc"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -154,6 +158,16 @@ def vp_run_slot_host(plan: int, H_host, C: int, sym_host, S: int, x_host, l_host
                      stream=None) -> None:
     _check(load().vp_run_slot_host(plan, _addr(H_host), int(C), _addr(sym_host), int(S), _addr(x_host),
                                    _addr(l_host), _addr(gamma_host), _stream(stream)), "vp_run_slot_host")
+
+
+def vp_precode_noalloc(plan: int, H, C: int, sym_idx, S: int, x, l, gamma, status=None, stream=None) -> None:
+    """One slot without any allocation (state in the library's static device array)."""
+    _check(load().vp_precode_noalloc(plan, _addr(H), int(C), _addr(sym_idx), int(S), _addr(x), _addr(l),
+                                     _addr(gamma), _addr(status), _stream(stream)), "vp_precode_noalloc")
+
+
+def vp_noalloc_capacity_bytes() -> int:
+    return int(load().vp_noalloc_capacity_bytes())
 
 
 def vp_last_launch_count(plan: int) -> int:

@@ -1,0 +1,104 @@
+// vp_precode_noalloc: one slot (factorise + select paths + precode) that
+// allocates nothing. It is meant for callers that cannot let a library call
+// cudaMalloc: real-time slot loops (cudaMalloc may synchronise the device and
+// take unbounded time inside a slot's deadline), processes whose device memory
+// is reserved up front by another allocator, and hosts that hand this library
+// device buffers only. The per-channel state that a plan would
+// keep in cudaMalloc'd memory lives instead in the file-scope array
+// g_noalloc_state below, sized for a fixed maximum; the kernels are the
+// plan path's own kernels, run on that storage.
+#include <mutex>
+
+#include "vp_internal.cuh"
+
+namespace {
+
+// 8 MiB of per-channel state. Every GPU that loads this library holds it
+// until the process exits.
+constexpr size_t kNoAllocBytes = size_t(8) << 20;
+__device__ __align__(256) unsigned char g_noalloc_state[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};   // device address of g_noalloc_state, per device
+
+// The host-side name g_noalloc_state is only a stand-in for the device array:
+// the address a kernel may use comes from cudaGetSymbolAddress, once per
+// device, with that device current.
+vp_status scratch_address(void** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_state) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return VP_ERR_CUDA;
+        }
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return VP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Lays the state of C channels out in the array; returns the bytes used.
+size_t carve(unsigned char* base, int C, int K, int M, int n, vp::DeviceState* d)
+{
+    const size_t nch = (size_t)vp::n_chunks(n);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* p = base ? base + off : nullptr;
+        off = align256(off + bytes);
+        return p;
+    };
+    d->utp = reinterpret_cast<float4*>(take(sizeof(float4) * C * K * K));
+    d->utc = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * K));
+    d->w = reinterpret_cast<float*>(take(sizeof(float) * C * K));
+    d->ul = take((size_t)C * K);
+    d->pt = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * M));
+    d->ptlo = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * M));
+    d->paths = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * n));
+    d->maxq = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * nch));
+    d->st = take((size_t)C);
+    d->nflag = reinterpret_cast<int*>(take(sizeof(int)));
+    d->flags = reinterpret_cast<int*>(take(sizeof(int) * C));
+    return off;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t vp_noalloc_capacity_bytes(void) { return kNoAllocBytes; }
+
+vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const uint8_t* sym_idx, int S, void* x,
+                             int8_t* l, float* gamma, uint8_t* status, void* stream)
+{
+    if (!plan || !H || !sym_idx || !x || !l || !gamma || C < 1 || S < 0) return VP_ERR_INVALID_ARG;
+    vp::DeviceState probe;
+    if (carve(nullptr, C, plan->K, plan->M, plan->n_paths, &probe) > kNoAllocBytes) return VP_ERR_CAPACITY;
+    void* base = nullptr;
+    vp_status st = scratch_address(&base);
+    if (st != VP_OK) return st;
+
+    vp_plan p = *plan;                    // parameters only; the state points into the array
+    carve(static_cast<unsigned char*>(base), C, p.K, p.M, p.n_paths, &p.d);
+    p.cap = C;
+    p.C = C;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float2* h = static_cast<const float2*>(H);
+    if (cudaMemsetAsync(p.d.nflag, 0, sizeof(int), s) != cudaSuccess) return VP_ERR_CUDA;
+    if (vp::launch_factor32(&p, h, C, nullptr, nullptr, nullptr, s) != cudaSuccess) return VP_ERR_CUDA;
+    if (vp::launch_factor64(&p, h, C, nullptr, nullptr, nullptr, s) != cudaSuccess) return VP_ERR_CUDA;
+    if (vp::launch_pathsel(&p, C, s) != cudaSuccess) return VP_ERR_CUDA;
+    if (status && cudaMemcpyAsync(status, p.d.st, (size_t)C, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return VP_ERR_CUDA;
+    if (S > 0 && vp::launch_search(&p, sym_idx, S, nullptr, C * S, static_cast<float2*>(x), l, gamma, s) != cudaSuccess)
+        return VP_ERR_CUDA;
+    return VP_OK;
+}
+
+}  // extern "C"
