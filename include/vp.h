@@ -87,8 +87,10 @@ typedef enum {
  */
 vp_status vp_plan_create(int K, int M, int qam, int n_paths, float tau, vp_plan** out);
 
-/* Channels whose kappa_hat = max_l R_ll^2 / min_l R_ll^2 (a lower bound on
- * cond(H H^H)) exceeds `kappa_hat` are re-factorised in FP64 on the GPU
+/* Channels whose kappa_hat = sigma_max(R)^2 sigma_max(U)^2, each largest
+ * singular value estimated by six power iterations on the FP32 factor (a
+ * lower bound on cond(H H^H) that is tight in practice), exceeds
+ * `kappa_hat` are re-factorised in FP64 on the GPU
  * (pivoted Cholesky of the FP64 Gram matrix and one Newton refinement of
  * U). 0 sends every channel to FP64; +inf none. Negative or NaN is invalid. */
 vp_status vp_plan_set_fp64_threshold(vp_plan* plan, float kappa_hat);
@@ -183,6 +185,78 @@ vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const ui
 
 /* Size in bytes of the static device array behind vp_precode_noalloc. */
 size_t vp_noalloc_capacity_bytes(void);
+
+/*
+ * Uneven batches: many independent problems of different shape in a few
+ * launches (the paper's many-users / many-cells setting, where every
+ * subcarrier or cell brings its own K x M channel, QAM order and path budget).
+ * A problem is one channel and its S data vectors; it goes through the same
+ * steps as vp_factorize + vp_precode (Alg. 1, Eq. mop, Alg. 2). The limits of
+ * each field are those of vp_plan_create.
+ */
+typedef struct {
+    int K, M, qam, n_paths;
+    float tau;               /* perturbation interval; 0 = 2 sqrt(qam) */
+    int S;                   /* data vectors of this problem (>= 0) */
+    const void* H;           /* complex64 [K][M] */
+    const uint8_t* sym_idx;  /* uint8 [S][K], QAM indices in user order */
+    void* x;                 /* complex64 [S][M] precoded vectors */
+    int8_t* l;               /* int8 [S][K][2] perturbation, user order */
+    float* gamma;            /* float [S] */
+    uint8_t* status;         /* optional uint8 [1]: VP_CH_* bits of the channel */
+} vp_problem_desc;
+
+typedef struct vp_batch vp_batch;
+
+/*
+ * Plan an uneven batch (host only; nothing is allocated on the device).
+ *   descs           HOST array [n_problems]; the device pointers it holds
+ *                   are captured and must stay valid while the batch is used
+ *   fp64_threshold  as vp_plan_set_fp64_threshold (1e4 is the default)
+ * Problems are grouped by kernel shape: one factor launch per (K, M), one
+ * path-selection launch per n_paths class (<= 16, 64, 256, 1024), one
+ * search launch per K class (<= 2, 4, 8, 12, 16), heaviest problems first.
+ * Returns VP_ERR_INVALID_ARG if any descriptor is out of range.
+ */
+vp_status vp_batch_create(const vp_problem_desc* descs, int n_problems, float fp64_threshold, vp_batch** out);
+
+/* Device workspace the batch needs: its problem table and the per-channel
+ * state (about 24 K^2 + 16 K M + 8 n_paths + 5 K bytes per problem). */
+size_t vp_batch_workspace_bytes(const vp_batch* batch);
+
+/*
+ * Bind the batch to a caller-owned device workspace of at least
+ * vp_batch_workspace_bytes bytes (16-byte aligned) and enqueue the upload of
+ * its problem table there. The table is copied from the batch's host memory
+ * (staged before the call returns). Call again after moving the workspace.
+ */
+vp_status vp_batch_bind(vp_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Run the whole batch: enqueue one memset and the grouped kernel launches
+ * (vp_batch_launch_count of them) on `stream`; no host synchronisation, no
+ * allocation and no host-to-device copy. Inputs are read and outputs written
+ * through the descriptors' pointers. Returns VP_ERR_NOT_FACTORIZED if the
+ * batch was never bound.
+ */
+vp_status vp_batch_launch(vp_batch* batch, void* stream);
+
+/* Kernel launches enqueued by one vp_batch_launch. */
+int vp_batch_launch_count(const vp_batch* batch);
+
+/* Free the batch (host memory only; the workspace stays the caller's). */
+vp_status vp_batch_destroy(vp_batch* batch);
+
+/*
+ * One-shot form: vp_batch_create (threshold 1e4) + vp_batch_bind +
+ * vp_batch_launch + vp_batch_destroy. `workspace_bytes` must be at least
+ * vp_precode_batch_workspace_bytes(descs, n_problems).
+ */
+vp_status vp_precode_batch(const vp_problem_desc* descs, int n_problems, size_t workspace_bytes, void* workspace,
+                           void* stream);
+
+/* Workspace of vp_precode_batch for these descriptors (0 if any is invalid). */
+size_t vp_precode_batch_workspace_bytes(const vp_problem_desc* descs, int n_problems);
 
 /* Number of kernel launches the last vp_factorize / vp_precode /
  * vp_run_slot_host call enqueued (copies and memsets not counted). */

@@ -23,7 +23,9 @@ __all__ = [
     "VPError", "load", "build", "library_path",
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize", "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
-    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_problem_desc", "vp_batch_create",
+    "vp_batch_workspace_bytes", "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy",
+    "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
     "EXPORTED_SYMBOLS", "Plan",
 ]
 
@@ -37,8 +39,18 @@ VP_MAX_PATHS = 1024
 EXPORTED_SYMBOLS = (
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize", "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
-    "vp_precode_noalloc", "vp_noalloc_capacity_bytes",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_batch_create", "vp_batch_workspace_bytes",
+    "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
+    "vp_precode_batch_workspace_bytes",
 )
+
+
+class vp_problem_desc(ctypes.Structure):
+    """One problem of an uneven batch (layout of the C struct)."""
+    _fields_ = [("K", ctypes.c_int), ("M", ctypes.c_int), ("qam", ctypes.c_int), ("n_paths", ctypes.c_int),
+                ("tau", ctypes.c_float), ("S", ctypes.c_int), ("H", ctypes.c_void_p), ("sym_idx", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("l", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
 
 _lock = threading.Lock()
 _lib = None
@@ -81,10 +93,23 @@ def load():
             L.vp_precode_noalloc.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp, vpp]
             L.vp_noalloc_capacity_bytes.argtypes = []
             L.vp_noalloc_capacity_bytes.restype = ctypes.c_size_t
+            descp = ctypes.POINTER(vp_problem_desc)
+            L.vp_batch_create.argtypes = [descp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(vpp)]
+            L.vp_batch_workspace_bytes.argtypes = [vpp]
+            L.vp_batch_workspace_bytes.restype = ctypes.c_size_t
+            L.vp_batch_bind.argtypes = [vpp, vpp, ctypes.c_size_t, vpp]
+            L.vp_batch_launch.argtypes = [vpp, vpp]
+            L.vp_batch_launch_count.argtypes = [vpp]
+            L.vp_batch_launch_count.restype = ctypes.c_int
+            L.vp_batch_destroy.argtypes = [vpp]
+            L.vp_precode_batch.argtypes = [descp, ctypes.c_int, ctypes.c_size_t, vpp, vpp]
+            L.vp_precode_batch_workspace_bytes.argtypes = [descp, ctypes.c_int]
+            L.vp_precode_batch_workspace_bytes.restype = ctypes.c_size_t
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
             for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize",
-                         "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_precode_noalloc"):
+                         "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_precode_noalloc", "vp_batch_create",
+                         "vp_batch_bind", "vp_batch_launch", "vp_batch_destroy", "vp_precode_batch"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -172,6 +197,112 @@ def vp_noalloc_capacity_bytes() -> int:
 
 def vp_last_launch_count(plan: int) -> int:
     return int(load().vp_last_launch_count(plan))
+
+
+def _desc_array(descs):
+    if isinstance(descs, ctypes.Array):
+        return descs
+    arr = (vp_problem_desc * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def vp_batch_create(descs, fp64_threshold: float = 1e4) -> int:
+    arr = _desc_array(descs)
+    out = ctypes.c_void_p()
+    _check(load().vp_batch_create(arr, len(arr), float(fp64_threshold), ctypes.byref(out)), "vp_batch_create")
+    return out.value
+
+
+def vp_batch_workspace_bytes(batch: int) -> int:
+    return int(load().vp_batch_workspace_bytes(batch))
+
+
+def vp_batch_bind(batch: int, workspace, workspace_bytes: int, stream=None) -> None:
+    _check(load().vp_batch_bind(batch, _addr(workspace), int(workspace_bytes), _stream(stream)), "vp_batch_bind")
+
+
+def vp_batch_launch(batch: int, stream=None) -> None:
+    _check(load().vp_batch_launch(batch, _stream(stream)), "vp_batch_launch")
+
+
+def vp_batch_launch_count(batch: int) -> int:
+    return int(load().vp_batch_launch_count(batch))
+
+
+def vp_batch_destroy(batch: int) -> None:
+    _check(load().vp_batch_destroy(batch), "vp_batch_destroy")
+
+
+def vp_precode_batch(descs, workspace, workspace_bytes: int, stream=None) -> None:
+    arr = _desc_array(descs)
+    _check(load().vp_precode_batch(arr, len(arr), int(workspace_bytes), _addr(workspace), _stream(stream)),
+           "vp_precode_batch")
+
+
+def vp_precode_batch_workspace_bytes(descs) -> int:
+    arr = _desc_array(descs)
+    return int(load().vp_precode_batch_workspace_bytes(arr, len(arr)))
+
+
+def problem_desc(K, M, qam, n_paths, H, sym_idx, x, l, gamma, status=None, tau=0.0, S=None) -> vp_problem_desc:
+    """Descriptor of one problem from tensors (S defaults to sym_idx's row count)."""
+    S = int(sym_idx.shape[0]) if S is None else int(S)
+    return vp_problem_desc(int(K), int(M), int(qam), int(n_paths), float(tau), S, _addr(H), _addr(sym_idx),
+                           _addr(x), _addr(l), _addr(gamma), _addr(status))
+
+
+def packed_descs(pk, H, sym, x, l, gamma, status=None, tau=0.0):
+    """Descriptors of packed problems (workloads.PackedProblems) whose flat
+    arrays live in the given device tensors (H, x complex64; sym uint8; l int8;
+    gamma float32; status uint8 [N] or None)."""
+    n = len(pk.K)
+    arr = (vp_problem_desc * n)()
+    hb, sb, xb, lb, gb = _addr(H), _addr(sym), _addr(x), _addr(l), _addr(gamma)
+    stb = _addr(status)
+    for i in range(n):
+        S = int(pk.S[i])
+        arr[i] = vp_problem_desc(int(pk.K[i]), int(pk.M[i]), int(pk.qam[i]), int(pk.n_paths[i]), float(tau), S,
+                                 hb + 8 * int(pk.H_off[i]), sb + int(pk.sym_off[i]) if S else None,
+                                 xb + 8 * int(pk.x_off[i]) if S else None, lb + int(pk.l_off[i]) if S else None,
+                                 gb + 4 * int(pk.g_off[i]) if S else None, stb + i if stb else None)
+    return arr
+
+
+class Batch:
+    """Owning handle of a vp_batch and its device workspace (a torch uint8 tensor)."""
+
+    def __init__(self, descs, fp64_threshold: float = 1e4, stream=None):
+        import torch
+        self.descs = _desc_array(descs)
+        self.handle = vp_batch_create(self.descs, fp64_threshold)
+        nbytes = vp_batch_workspace_bytes(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        self.ws_addr = (base + 255) // 256 * 256
+        vp_batch_bind(self.handle, self.ws_addr, nbytes, stream)
+        self.launches = vp_batch_launch_count(self.handle)
+
+    def launch(self, stream=None):
+        vp_batch_launch(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            vp_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

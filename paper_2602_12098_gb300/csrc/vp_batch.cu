@@ -1,0 +1,295 @@
+// Uneven batches: many independent problems (one channel and its data
+// vectors each) of different K x M, QAM order, path budget and tau, run by
+// the same kernels as a plan, in a few grouped launches.
+//
+// Grouping. The factor kernel keeps two channels in one warp (16 lanes each)
+// and loops over K and M with shuffles, so one launch holds one (K, M). Path
+// selection sizes its shared lists by n_paths: one launch per class
+// n <= 16, 64, 256, 1024. The search is templated on a K tile: one launch
+// per K <= 2, 4, 8, 12, 16. Inside a launch the problems run heaviest first
+// (S * n * K^2), so the long blocks start early and the short ones fill the
+// tail. The FP64 fix-up runs once over the channels all factor launches
+// flagged.
+//
+// Workspace (caller-owned device memory): the problem table, the three
+// launch orders, the FP64 list and every problem's resident state.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "vp_internal.cuh"
+
+struct vp_batch {
+    struct Group {
+        int stage;   // 0 factor, 1 paths, 2 search
+        int start, count;
+        int K, M, KT, n_max, km_max, s_max;
+    };
+    std::vector<vp_problem_desc> descs;
+    std::vector<vp::BatchProblem> table;   // device pointers filled in by bind
+    std::vector<int> ids;                  // [3][n]: factor, paths, search order
+    std::vector<size_t> state_off;         // per problem, from the state base
+    std::vector<Group> groups;
+    float kappa_thr = 1e4f;
+    size_t off_table = 0, off_ids = 0, off_nflag = 0, off_flags = 0, off_state = 0, bytes = 0;
+    unsigned char* ws = nullptr;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Per-problem state, in the order utp, utc, pt, ptlo, paths, maxq, w, ul, st.
+size_t state_bytes(int K, int M, int n)
+{
+    size_t b = 16 * (size_t)K * K;
+    b += 8 * (size_t)K * K + 16 * (size_t)K * M + 8 * (size_t)n + 8 * (size_t)vp::n_chunks(n);
+    b += 4 * (size_t)K + (size_t)K + 1;
+    return align_up(b, 16);
+}
+
+bool desc_ok(const vp_problem_desc& d)
+{
+    if (!vp::shape_ok(d.K, d.M, d.qam, d.n_paths, d.tau) || d.S < 0 || !d.H) return false;
+    if (d.S > 0 && (!d.sym_idx || !d.x || !d.l || !d.gamma)) return false;
+    return true;
+}
+
+int k_tile(int K) { return K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16; }
+int n_class(int n) { return n <= 16 ? 16 : n <= 64 ? 64 : n <= 256 ? 256 : 1024; }
+
+vp_status plan_batch(const vp_problem_desc* descs, int n, float thr, vp_batch* b)
+{
+    b->descs.assign(descs, descs + n);
+    b->kappa_thr = thr;
+    const size_t N = (size_t)n;
+    b->ids.assign(3 * N, 0);
+    b->state_off.assign(N, 0);
+    size_t st = 0;
+    for (size_t i = 0; i < N; ++i) {
+        b->state_off[i] = st;
+        st += state_bytes(descs[i].K, descs[i].M, descs[i].n_paths);
+    }
+    auto cost = [&](int i) {
+        const vp_problem_desc& d = descs[i];
+        return (double)d.S * d.n_paths * d.K * d.K + 1.0;
+    };
+    std::vector<int> idx(N);
+    for (size_t i = 0; i < N; ++i) idx[i] = (int)i;
+
+    // stage 0: factor, grouped by (K, M)
+    std::vector<int> o = idx;
+    std::stable_sort(o.begin(), o.end(), [&](int a, int c) {
+        if (descs[a].K != descs[c].K) return descs[a].K > descs[c].K;
+        return descs[a].M > descs[c].M;
+    });
+    for (size_t i = 0; i < N;) {
+        size_t j = i;
+        while (j < N && descs[o[j]].K == descs[o[i]].K && descs[o[j]].M == descs[o[i]].M) ++j;
+        vp_batch::Group g = {0, (int)i, (int)(j - i), descs[o[i]].K, descs[o[i]].M, 0, 0, 0, 0};
+        b->groups.push_back(g);
+        i = j;
+    }
+    std::copy(o.begin(), o.end(), b->ids.begin());
+
+    // stage 1: paths, grouped by n class, heaviest first inside
+    o = idx;
+    std::stable_sort(o.begin(), o.end(), [&](int a, int c) {
+        const int ca = n_class(descs[a].n_paths), cc = n_class(descs[c].n_paths);
+        if (ca != cc) return ca > cc;
+        return (long long)descs[a].n_paths * descs[a].K > (long long)descs[c].n_paths * descs[c].K;
+    });
+    for (size_t i = 0; i < N;) {
+        size_t j = i;
+        int nmax = 0;
+        while (j < N && n_class(descs[o[j]].n_paths) == n_class(descs[o[i]].n_paths)) {
+            nmax = std::max(nmax, descs[o[j]].n_paths);
+            ++j;
+        }
+        vp_batch::Group g = {1, (int)i, (int)(j - i), 0, 0, 0, nmax, 0, 0};
+        b->groups.push_back(g);
+        i = j;
+    }
+    std::copy(o.begin(), o.end(), b->ids.begin() + N);
+
+    // stage 2: search, grouped by K tile, heaviest first inside
+    o = idx;
+    std::stable_sort(o.begin(), o.end(), [&](int a, int c) {
+        const int ta = k_tile(descs[a].K), tc = k_tile(descs[c].K);
+        if (ta != tc) return ta > tc;
+        return cost(a) > cost(c);
+    });
+    for (size_t i = 0; i < N;) {
+        size_t j = i;
+        int nmax = 0, km = 0, smax = 0;
+        while (j < N && k_tile(descs[o[j]].K) == k_tile(descs[o[i]].K)) {
+            const vp_problem_desc& d = descs[o[j]];
+            nmax = std::max(nmax, d.n_paths);
+            km = std::max(km, d.K * d.M);
+            smax = std::max(smax, d.S);
+            ++j;
+        }
+        vp_batch::Group g = {2, (int)i, (int)(j - i), 0, 0, k_tile(descs[o[i]].K), nmax, km, smax};
+        b->groups.push_back(g);
+        i = j;
+    }
+    std::copy(o.begin(), o.end(), b->ids.begin() + 2 * N);
+
+    b->off_table = 0;
+    b->off_ids = align_up(sizeof(vp::BatchProblem) * N, 256);
+    b->off_nflag = b->off_ids + align_up(sizeof(int) * 3 * N, 256);
+    b->off_flags = b->off_nflag + 256;
+    b->off_state = b->off_flags + align_up(sizeof(int) * N, 256);
+    b->bytes = b->off_state + st;
+    return VP_OK;
+}
+
+void fill_table(vp_batch* b)
+{
+    const size_t N = b->descs.size();
+    b->table.resize(N);
+    unsigned char* base = b->ws + b->off_state;
+    for (size_t i = 0; i < N; ++i) {
+        const vp_problem_desc& d = b->descs[i];
+        vp::BatchProblem& p = b->table[i];
+        const int K = d.K, M = d.M, n = d.n_paths;
+        unsigned char* q = base + b->state_off[i];
+        p.utp = reinterpret_cast<float4*>(q);
+        q += 16 * (size_t)K * K;
+        p.utc = reinterpret_cast<float2*>(q);
+        q += 8 * (size_t)K * K;
+        p.pt = reinterpret_cast<float2*>(q);
+        q += 8 * (size_t)K * M;
+        p.ptlo = reinterpret_cast<float2*>(q);
+        q += 8 * (size_t)K * M;
+        p.paths = reinterpret_cast<uint64_t*>(q);
+        q += 8 * (size_t)n;
+        p.maxq = reinterpret_cast<uint64_t*>(q);
+        q += 8 * (size_t)vp::n_chunks(n);
+        p.w = reinterpret_cast<float*>(q);
+        q += 4 * (size_t)K;
+        p.ul = q;
+        q += K;
+        p.st = q;
+        p.H = static_cast<const float2*>(d.H);
+        p.sym = d.sym_idx;
+        p.x = static_cast<float2*>(d.x);
+        p.l = d.l;
+        p.gamma = d.gamma;
+        p.status = d.status;
+        p.K = K;
+        p.M = M;
+        p.n = n;
+        p.m_qam = vp::qam_side(d.qam);
+        p.S = d.S;
+        p.tau = (d.tau == 0.f) ? 2.0f * std::sqrt((float)d.qam) : d.tau;
+        p.kappa_thr = b->kappa_thr;
+        p.pad_ = 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_batch_create(const vp_problem_desc* descs, int n_problems, float fp64_threshold, vp_batch** out)
+{
+    if (!out) return VP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!descs || n_problems < 1 || std::isnan(fp64_threshold) || fp64_threshold < 0.f) return VP_ERR_INVALID_ARG;
+    for (int i = 0; i < n_problems; ++i)
+        if (!desc_ok(descs[i])) return VP_ERR_INVALID_ARG;
+    vp_batch* b = new (std::nothrow) vp_batch();
+    if (!b) return VP_ERR_OOM;
+    try {
+        plan_batch(descs, n_problems, fp64_threshold, b);
+    } catch (...) {
+        delete b;
+        return VP_ERR_OOM;
+    }
+    *out = b;
+    return VP_OK;
+}
+
+size_t vp_batch_workspace_bytes(const vp_batch* b) { return b ? b->bytes : 0; }
+
+vp_status vp_batch_bind(vp_batch* b, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!b || !workspace || workspace_bytes < b->bytes || (reinterpret_cast<uintptr_t>(workspace) & 15u))
+        return VP_ERR_INVALID_ARG;
+    b->ws = static_cast<unsigned char*>(workspace);
+    try {
+        fill_table(b);
+    } catch (...) {
+        b->ws = nullptr;
+        return VP_ERR_OOM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t N = b->descs.size();
+    if (cudaMemcpyAsync(b->ws + b->off_table, b->table.data(), sizeof(vp::BatchProblem) * N, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(b->ws + b->off_ids, b->ids.data(), sizeof(int) * 3 * N, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+        b->ws = nullptr;
+        return VP_ERR_CUDA;
+    }
+    return VP_OK;
+}
+
+vp_status vp_batch_launch(vp_batch* b, void* stream)
+{
+    if (!b) return VP_ERR_INVALID_ARG;
+    if (!b->ws) return VP_ERR_NOT_FACTORIZED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int N = (int)b->descs.size();
+    const vp::BatchProblem* probs = reinterpret_cast<const vp::BatchProblem*>(b->ws + b->off_table);
+    const int* ids = reinterpret_cast<const int*>(b->ws + b->off_ids);
+    int* nflag = reinterpret_cast<int*>(b->ws + b->off_nflag);
+    int* flags = reinterpret_cast<int*>(b->ws + b->off_flags);
+    if (cudaMemsetAsync(nflag, 0, sizeof(int), s) != cudaSuccess) return VP_ERR_CUDA;
+    for (const vp_batch::Group& g : b->groups)
+        if (g.stage == 0 &&
+            vp::launch_factor32_batch(probs, ids + g.start, g.count, g.K, g.M, nflag, flags, s) != cudaSuccess)
+            return VP_ERR_CUDA;
+    if (vp::launch_factor64_batch(probs, nflag, flags, N, s) != cudaSuccess) return VP_ERR_CUDA;
+    for (const vp_batch::Group& g : b->groups)
+        if (g.stage == 1 && vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, s) != cudaSuccess)
+            return VP_ERR_CUDA;
+    for (const vp_batch::Group& g : b->groups)
+        if (g.stage == 2 && vp::launch_search_batch(probs, ids + 2 * N + g.start, g.count, g.KT, g.km_max, g.n_max,
+                                                    g.s_max, s) != cudaSuccess)
+            return VP_ERR_CUDA;
+    return VP_OK;
+}
+
+int vp_batch_launch_count(const vp_batch* b) { return b ? (int)b->groups.size() + 1 : 0; }
+
+vp_status vp_batch_destroy(vp_batch* b)
+{
+    delete b;
+    return VP_OK;
+}
+
+size_t vp_precode_batch_workspace_bytes(const vp_problem_desc* descs, int n_problems)
+{
+    vp_batch* b = nullptr;
+    if (vp_batch_create(descs, n_problems, 1e4f, &b) != VP_OK) return 0;
+    const size_t bytes = b->bytes;
+    vp_batch_destroy(b);
+    return bytes;
+}
+
+vp_status vp_precode_batch(const vp_problem_desc* descs, int n_problems, size_t workspace_bytes, void* workspace,
+                           void* stream)
+{
+    vp_batch* b = nullptr;
+    vp_status st = vp_batch_create(descs, n_problems, 1e4f, &b);
+    if (st != VP_OK) return st;
+    st = vp_batch_bind(b, workspace, workspace_bytes, stream);
+    if (st == VP_OK) st = vp_batch_launch(b, stream);
+    vp_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"

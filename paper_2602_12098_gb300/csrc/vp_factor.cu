@@ -27,13 +27,49 @@ constexpr unsigned kFull = 0xffffffffu;
 
 struct FactorArgs {
     const float2* H;
-    int C, K, M;
+    int C, K, M, n;
     float kappa_thr;
     DeviceState d;
     float2* U_out;
     float2* P_out;
     uint8_t* ul_out;
+    // batch mode (probs != null): channel i of the launch is problem ids[i] of
+    // the table; its state lives in the workspace, no U / P / ul outputs
+    const BatchProblem* probs;
+    const int* ids;
+    const int* nflag_in;   // FP64 list (batch: in the workspace; plain: d.nflag / d.flags)
+    int* nflag;
+    int* flags;
 };
+
+// Inputs and outputs of one channel.
+struct FChan {
+    const float2* H;   // [K][M]
+    ChanState s;
+    float2* U_out;     // [K][K] or null
+    float2* P_out;     // [M][K] or null
+    uint8_t* ul_out;   // [K] or null
+};
+
+__device__ __forceinline__ FChan fchan(const FactorArgs& a, int c, int K, int M)
+{
+    FChan f;
+    if (a.probs) {
+        const BatchProblem& p = a.probs[c];
+        f.H = p.H;
+        f.s = chan_state(p);
+        f.U_out = nullptr;
+        f.P_out = nullptr;
+        f.ul_out = nullptr;
+    } else {
+        f.H = a.H + (size_t)c * K * M;
+        f.s = chan_state(a.d, (size_t)c, K, M, a.n);
+        f.U_out = a.U_out ? a.U_out + (size_t)c * K * K : nullptr;
+        f.P_out = a.P_out ? a.P_out + (size_t)c * M * K : nullptr;
+        f.ul_out = a.ul_out ? a.ul_out + (size_t)c * K : nullptr;
+    }
+    return f;
+}
 
 template <int MT>
 struct Smem32 {
@@ -47,23 +83,22 @@ struct Smem32 {
     int piv[kMaxK];            // user pivoted at step t
 };
 
-__device__ __forceinline__ void write_channel_outputs_zero(const FactorArgs& a, int c, int j)
+__device__ __forceinline__ void write_channel_outputs_zero(const FChan& f, int K, int M, int j)
 {
-    const int K = a.K, M = a.M;
     if (j < K) {
         for (int k = 0; k < K; ++k) {
-            a.d.utp[((size_t)c * K + j) * K + k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            a.d.utc[((size_t)c * K + j) * K + k] = make_float2(0.f, 0.f);
-            if (a.U_out) a.U_out[((size_t)c * K + j) * K + k] = make_float2(0.f, 0.f);
+            f.s.utp[j * K + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            f.s.utc[j * K + k] = make_float2(0.f, 0.f);
+            if (f.U_out) f.U_out[j * K + k] = make_float2(0.f, 0.f);
         }
         for (int m = 0; m < M; ++m) {
-            a.d.pt[((size_t)c * K + j) * M + m] = make_float2(0.f, 0.f);
-            a.d.ptlo[((size_t)c * K + j) * M + m] = make_float2(0.f, 0.f);
-            if (a.P_out) a.P_out[((size_t)c * M + m) * K + j] = make_float2(0.f, 0.f);
+            f.s.pt[j * M + m] = make_float2(0.f, 0.f);
+            f.s.ptlo[j * M + m] = make_float2(0.f, 0.f);
+            if (f.P_out) f.P_out[m * K + j] = make_float2(0.f, 0.f);
         }
-        a.d.w[(size_t)c * K + j] = 0.f;
-        a.d.ul[(size_t)c * K + j] = (uint8_t)j;
-        if (a.ul_out) a.ul_out[(size_t)c * K + j] = (uint8_t)j;
+        f.s.w[j] = 0.f;
+        f.s.ul[j] = (uint8_t)j;
+        if (f.ul_out) f.ul_out[j] = (uint8_t)j;
     }
 }
 
@@ -108,9 +143,11 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     const int j = threadIdx.x % kLanes;
     const int hw = (threadIdx.x >> 4) & 1;                 // half of the warp
     const unsigned hmask = 0xFFFFu << (16 * hw);
-    const int c = blockIdx.x * kChPerBlock32 + slot;
-    const bool valid = c < a.C;
+    const int ci = blockIdx.x * kChPerBlock32 + slot;
+    const bool valid = ci < a.C;
     const int K = a.K, M = a.M;
+    const int c = valid ? (a.ids ? a.ids[ci] : ci) : 0;   // channel (plain) or table index (batch)
+    const FChan f = fchan(a, c, K, M);
     const bool act = j < K;
     Smem32<MT>& sm = smem[slot];
 
@@ -120,7 +157,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
         float2 h = make_float2(0.f, 0.f);
-        if (valid && act && m < M) h = a.H[((size_t)c * K + j) * M + m];
+        if (valid && act && m < M) h = f.H[j * M + m];
         finite = finite && isfinite(h.x) && isfinite(h.y);
         av[m] = make_float2(h.x, -h.y);
     }
@@ -236,19 +273,20 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     // channels above the plan threshold (or degenerate) go to the FP64 path
     const float kappa = power_sigma2(sm.rl, K, j) * power_sigma2(sm.uu, K, j);
     const bool degen = (__ballot_sync(kFull, degenerate) & hmask) != 0u;
-    const bool to64 = !nonfinite && (degen || !(kappa <= a.kappa_thr));
+    const float thr = (a.probs && valid) ? a.probs[c].kappa_thr : a.kappa_thr;
+    const bool to64 = !nonfinite && (degen || !(kappa <= thr));
     if (!valid) return;
 
     if (nonfinite) {
-        write_channel_outputs_zero(a, c, j);
-        if (j == 0) a.d.st[c] = (uint8_t)VP_CH_NONFINITE;
+        write_channel_outputs_zero(f, K, M, j);
+        if (j == 0) f.s.st[0] = (uint8_t)VP_CH_NONFINITE;
         return;
     }
     if (to64) {
         if (j == 0) {
-            const int idx = atomicAdd(a.d.nflag, 1);
-            a.d.flags[idx] = c;
-            a.d.st[c] = (uint8_t)VP_CH_FP64;
+            const int idx = atomicAdd(a.nflag, 1);
+            a.flags[idx] = c;
+            f.s.st[0] = (uint8_t)VP_CH_FP64;
         }
         return;
     }
@@ -257,17 +295,17 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
         const int i = j;
         const float rii = sm.rl[i][i].x;
         const float uii = sm.uu[i][i].x;
-        a.d.w[(size_t)c * K + i] = uii * uii;
+        f.s.w[i] = uii * uii;
         const uint8_t ui = (uint8_t)sm.piv[K - 1 - i];
-        a.d.ul[(size_t)c * K + i] = ui;
-        if (a.ul_out) a.ul_out[(size_t)c * K + i] = ui;
+        f.s.ul[i] = ui;
+        if (f.ul_out) f.ul_out[i] = ui;
         for (int k = 0; k < K; ++k) {
             float2 u = sm.uu[i][k];
             float2 ut = (k > i) ? make_float2(u.x * rii, u.y * rii)
                                 : (k == i ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
-            a.d.utp[((size_t)c * K + i) * K + k] = make_float4(ut.x, ut.y, ut.y, ut.x);
-            a.d.utc[((size_t)c * K + k) * K + i] = ut;
-            if (a.U_out) a.U_out[((size_t)c * K + i) * K + k] = u;
+            f.s.utp[i * K + k] = make_float4(ut.x, ut.y, ut.y, ut.x);
+            f.s.utc[k * K + i] = ut;
+            if (f.U_out) f.U_out[i * K + k] = u;
         }
     }
 
@@ -299,13 +337,13 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 #pragma unroll
         for (int m = 0; m < MT; ++m) {
             if (m < M) {
-                a.d.pt[((size_t)c * K + u) * M + m] = z[m];
-                a.d.ptlo[((size_t)c * K + u) * M + m] = make_float2(0.f, 0.f);
-                if (a.P_out) a.P_out[((size_t)c * M + m) * K + u] = z[m];
+                f.s.pt[u * M + m] = z[m];
+                f.s.ptlo[u * M + m] = make_float2(0.f, 0.f);
+                if (f.P_out) f.P_out[m * K + u] = z[m];
             }
         }
     }
-    if (j == 0) a.d.st[c] = 0;
+    if (j == 0) f.s.st[0] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -361,12 +399,14 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
     __shared__ Smem64 smem[kW64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Smem64& sm = smem[warp];
-    const int K = a.K, M = a.M;
-    const int nflag = *a.d.nflag;
+    const int nflag = *a.nflag_in;
 
     for (int slot = blockIdx.x * kW64 + warp; slot < nflag; slot += gridDim.x * kW64) {
-        const int c = a.d.flags[slot];
-        for (int i = lane; i < K * M; i += 32) sm.h[i / M][i % M] = a.H[(size_t)c * K * M + i];
+        const int c = a.flags[slot];
+        const int K = a.probs ? a.probs[c].K : a.K;
+        const int M = a.probs ? a.probs[c].M : a.M;
+        const FChan f = fchan(a, c, K, M);
+        for (int i = lane; i < K * M; i += 32) sm.h[i / M][i % M] = f.H[i];
         if (lane < K) sm.rem[lane] = lane;
         __syncwarp();
         // Gram matrix (compensated FP32, exact for FP32 input), both triangles in FP64
@@ -496,13 +536,13 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 const double urr = sm.lc[r][r].x;
                 const float2 ut = (q > r) ? make_float2((float)(v.x / urr), (float)(v.y / urr))
                                           : (q == r ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
-                a.d.utp[((size_t)c * K + r) * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
-                a.d.utc[((size_t)c * K + q) * K + r] = ut;
-                if (a.U_out) a.U_out[((size_t)c * K + r) * K + q] = make_float2(hx, hy);
+                f.s.utp[r * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
+                f.s.utc[q * K + r] = ut;
+                if (f.U_out) f.U_out[r * K + q] = make_float2(hx, hy);
                 if (q == 0) {
-                    a.d.w[(size_t)c * K + r] = (float)(urr * urr);
-                    a.d.ul[(size_t)c * K + r] = (uint8_t)sm.uol[r];
-                    if (a.ul_out) a.ul_out[(size_t)c * K + r] = (uint8_t)sm.uol[r];
+                    f.s.w[r] = (float)(urr * urr);
+                    f.s.ul[r] = (uint8_t)sm.uol[r];
+                    if (f.ul_out) f.ul_out[r] = (uint8_t)sm.uol[r];
                 }
             }
             __syncwarp();
@@ -537,14 +577,14 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
                 const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
                 const int uk = sm.uol[k];
-                a.d.pt[((size_t)c * K + uk) * M + m] = hi;
-                a.d.ptlo[((size_t)c * K + uk) * M + m] = lo;
-                if (a.P_out) a.P_out[((size_t)c * M + m) * K + uk] = hi;
+                f.s.pt[uk * M + m] = hi;
+                f.s.ptlo[uk * M + m] = lo;
+                if (f.P_out) f.P_out[m * K + uk] = hi;
             }
-            if (lane == 0) a.d.st[c] = (uint8_t)VP_CH_FP64;
+            if (lane == 0) f.s.st[0] = (uint8_t)VP_CH_FP64;
         } else {
-            if (lane < 16) write_channel_outputs_zero(a, c, lane);
-            if (lane == 0) a.d.st[c] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
+            if (lane < 16) write_channel_outputs_zero(f, K, M, lane);
+            if (lane == 0) f.s.st[0] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
         }
         __syncwarp();
     }
@@ -557,12 +597,37 @@ FactorArgs make_args(const vp_plan* p, const float2* H, int C, float2* U_out, fl
     a.C = C;
     a.K = p->K;
     a.M = p->M;
+    a.n = p->n_paths;
     a.kappa_thr = p->kappa_thr;
     a.d = p->d;
     a.U_out = U_out;
     a.P_out = P_out;
     a.ul_out = ul_out;
+    a.probs = nullptr;
+    a.ids = nullptr;
+    a.nflag_in = p->d.nflag;
+    a.nflag = p->d.nflag;
+    a.flags = p->d.flags;
     return a;
+}
+
+cudaError_t run_factor32(const FactorArgs& a, cudaStream_t s)
+{
+    const int blocks = (a.C + kChPerBlock32 - 1) / kChPerBlock32;
+    const int threads = kLanes * kChPerBlock32;
+    if (a.M <= 4) factor32_kernel<4><<<blocks, threads, 0, s>>>(a);
+    else if (a.M <= 8) factor32_kernel<8><<<blocks, threads, 0, s>>>(a);
+    else factor32_kernel<16><<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t run_factor64(const FactorArgs& a, int max_flagged, cudaStream_t s)
+{
+    int blocks = (max_flagged + kW64 - 1) / kW64;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    factor64_kernel<<<blocks, 32 * kW64, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -570,23 +635,39 @@ FactorArgs make_args(const vp_plan* p, const float2* H, int C, float2* U_out, fl
 cudaError_t launch_factor32(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
                             uint8_t* ul_out, cudaStream_t s)
 {
-    const FactorArgs a = make_args(p, H, C, U_out, P_out, ul_out);
-    const int blocks = (C + kChPerBlock32 - 1) / kChPerBlock32;
-    const int threads = kLanes * kChPerBlock32;
-    if (p->M <= 4) factor32_kernel<4><<<blocks, threads, 0, s>>>(a);
-    else if (p->M <= 8) factor32_kernel<8><<<blocks, threads, 0, s>>>(a);
-    else factor32_kernel<16><<<blocks, threads, 0, s>>>(a);
-    return cudaGetLastError();
+    return run_factor32(make_args(p, H, C, U_out, P_out, ul_out), s);
 }
 
 cudaError_t launch_factor64(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
                             uint8_t* ul_out, cudaStream_t s)
 {
-    const FactorArgs a = make_args(p, H, C, U_out, P_out, ul_out);
-    int blocks = (C + kW64 - 1) / kW64;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    factor64_kernel<<<blocks, 32 * kW64, 0, s>>>(a);
-    return cudaGetLastError();
+    return run_factor64(make_args(p, H, C, U_out, P_out, ul_out), C, s);
+}
+
+cudaError_t launch_factor32_batch(const BatchProblem* probs, const int* ids, int count, int K, int M,
+                                  int* nflag, int* flags, cudaStream_t s)
+{
+    FactorArgs a = FactorArgs();
+    a.C = count;
+    a.K = K;
+    a.M = M;
+    a.kappa_thr = 0.f;   // per problem, read from the table
+    a.probs = probs;
+    a.ids = ids;
+    a.nflag_in = nflag;
+    a.nflag = nflag;
+    a.flags = flags;
+    return run_factor32(a, s);
+}
+
+cudaError_t launch_factor64_batch(const BatchProblem* probs, const int* nflag, const int* flags, int max_flagged,
+                                  cudaStream_t s)
+{
+    FactorArgs a = FactorArgs();
+    a.probs = probs;
+    a.nflag_in = nflag;
+    a.flags = const_cast<int*>(flags);
+    return run_factor64(a, max_flagged, s);
 }
 
 }  // namespace vp

@@ -27,6 +27,75 @@ struct DeviceState {
     int* flags = nullptr;      // [cap]       their indices
 };
 
+// One problem of an uneven batch (one channel and its S data vectors), as
+// the kernels read it from the device table of vp_precode_batch. The state
+// pointers point into the batch workspace.
+struct BatchProblem {
+    const float2* H;      // [K][M]
+    const uint8_t* sym;   // [S][K]
+    float2* x;            // [S][M]
+    int8_t* l;            // [S][K][2]
+    float* gamma;         // [S]
+    uint8_t* status;      // [1] or null
+    float4* utp;
+    float2* utc;
+    float* w;
+    uint8_t* ul;
+    float2* pt;
+    float2* ptlo;
+    uint64_t* paths;
+    uint64_t* maxq;
+    uint8_t* st;
+    int K, M, n, m_qam, S;
+    float tau, kappa_thr;
+    int pad_;
+};
+
+// Resident state of one channel (pointers offset to that channel).
+struct ChanState {
+    float4* utp;
+    float2* utc;
+    float* w;
+    uint8_t* ul;
+    float2* pt;
+    float2* ptlo;
+    uint64_t* paths;
+    uint64_t* maxq;
+    uint8_t* st;
+};
+
+__host__ __device__ inline int n_chunks(int n_paths) { return (n_paths + 31) / 32; }
+
+__host__ __device__ inline ChanState chan_state(const DeviceState& d, size_t c, int K, int M, int n)
+{
+    ChanState s;
+    s.utp = d.utp + c * K * K;
+    s.utc = d.utc + c * K * K;
+    s.w = d.w + c * K;
+    s.ul = d.ul + c * K;
+    s.pt = d.pt + c * K * M;
+    s.ptlo = d.ptlo + c * K * M;
+    s.paths = d.paths + c * n;
+    s.maxq = d.maxq + c * n_chunks(n);
+    s.st = d.st + c;
+    return s;
+}
+
+__host__ __device__ inline ChanState chan_state(const BatchProblem& p)
+{
+    ChanState s;
+    s.utp = p.utp;
+    s.utc = p.utc;
+    s.w = p.w;
+    s.ul = p.ul;
+    s.pt = p.pt;
+    s.ptlo = p.ptlo;
+    s.paths = p.paths;
+    s.maxq = p.maxq;
+    s.st = p.st;
+    return s;
+}
+
 }  // namespace vp
 
 struct vp_plan {
@@ -47,7 +116,23 @@ struct vp_plan {
 
 namespace vp {
 
-inline int n_chunks(int n_paths) { return (n_paths + 31) / 32; }
+// Limits of one problem shape (those of vp_plan_create).
+inline bool shape_ok(int K, int M, int qam, int n_paths, float tau)
+{
+    if (K < 1 || K > VP_MAX_K || M < K || M > VP_MAX_M) return false;
+    if (!(qam == 4 || qam == 16 || qam == 64 || qam == 256)) return false;
+    long long p9 = 1;
+    for (int i = 0; i < K && p9 <= VP_MAX_PATHS; ++i) p9 *= 9;
+    if (n_paths < 1 || n_paths > VP_MAX_PATHS || (long long)n_paths > p9) return false;
+    return tau >= 0.f && tau < 3.0e38f;
+}
+
+inline int qam_side(int qam)
+{
+    int m = 1;
+    while (m * m < qam) ++m;
+    return m;
+}
 
 // Kernel launchers (each returns cudaSuccess or the launch error).
 cudaError_t launch_factor32(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
@@ -57,6 +142,21 @@ cudaError_t launch_factor64(const vp_plan* p, const float2* H, int C, float2* U_
 cudaError_t launch_pathsel(const vp_plan* p, int C, cudaStream_t s);
 cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int32_t* vec_off,
                           int n_vec, float2* x, int8_t* l, float* gamma, cudaStream_t s);
+
+// Batch launchers: `ids[0..count)` are indices into the device table `probs`.
+// factor32: every listed problem has this K and M. FP64 candidates are
+// appended (as table indices) to flags / nflag.
+cudaError_t launch_factor32_batch(const BatchProblem* probs, const int* ids, int count, int K, int M,
+                                  int* nflag, int* flags, cudaStream_t s);
+// factor64: the problems listed in flags[0..*nflag); at most max_flagged of them.
+cudaError_t launch_factor64_batch(const BatchProblem* probs, const int* nflag, const int* flags, int max_flagged,
+                                  cudaStream_t s);
+// pathsel: every listed problem has n_paths <= n_max.
+cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int count, int n_max, cudaStream_t s);
+// search: every listed problem has K <= KT (KT in {2, 4, 8, 12, 16}) and the
+// given maxima of K*M, n_paths and S.
+cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int count, int KT, int km_max,
+                                int n_max, int s_max, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small device helpers shared by the kernels of this library.

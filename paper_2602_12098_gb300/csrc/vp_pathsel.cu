@@ -27,7 +27,10 @@ constexpr unsigned kFull = 0xffffffffu;
 
 struct PathArgs {
     int C, K, n, nch;
+    int ns;                     // skewed list length of the launch's largest n
     DeviceState d;
+    const BatchProblem* probs;  // batch mode: channel i of the launch is problem ids[i]
+    const int* ids;
 };
 
 // Shared-memory lists use a skewed index (one pad word per 8 entries): the
@@ -88,28 +91,38 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
     extern __shared__ uint64_t shm[];
     __shared__ uint64_t qws[8][kMaxK];
     __shared__ int ords[8][kMaxK];
-    const int n = a.n, K = a.K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * cpb + warp;
-    if (c >= a.C) return;
+    const int ci = blockIdx.x * cpb + warp;
+    if (ci >= a.C) return;
+    int n = a.n, K = a.K, nch = a.nch;
+    ChanState cs;
+    if (a.probs) {
+        const BatchProblem& p = a.probs[a.ids[ci]];
+        n = p.n;
+        K = p.K;
+        nch = n_chunks(n);
+        cs = chan_state(p);
+    } else {
+        cs = chan_state(a.d, (size_t)ci, K, 0, n);
+    }
     const int ns = sk(n);                                        // skewed length of one list
-    uint64_t* base = shm + (size_t)warp * 6 * ns;
+    uint64_t* base = shm + (size_t)warp * 6 * a.ns;
     // buffer b (0..2): metrics at base + 2 b ns, codes at base + (2 b + 1) ns
     // (pointer arithmetic: an indexed pointer array would live in local memory)
 #define BM(b) (base + 2 * (b) * ns)
 #define BC(b) (base + (2 * (b) + 1) * ns)
     uint64_t* qw = qws[warp];
     int* ord = ords[warp];
-    uint64_t* out = a.d.paths + (size_t)c * n;
-    uint64_t* mqo = a.d.maxq + (size_t)c * a.nch;
+    uint64_t* out = cs.paths;
+    uint64_t* mqo = cs.maxq;
 
-    if (a.d.st[c] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
+    if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
         for (int i = lane; i < n; i += 32) out[i] = 0;
-        for (int i = lane; i < a.nch; i += 32) mqo[i] = 0;
+        for (int i = lane; i < nch; i += 32) mqo[i] = 0;
         return;
     }
     {
-        const float wl = lane < K ? a.d.w[(size_t)c * K + lane] : 0.f;
+        const float wl = lane < K ? cs.w[lane] : 0.f;
         float wmax = wl;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(kFull, wmax, o));
@@ -120,7 +133,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         if (lane < K) {
             int rank = 0;
             for (int k = 0; k < K; ++k) {
-                const float wk = a.d.w[(size_t)c * K + k];
+                const float wk = cs.w[k];
                 rank += (wk < wl) || (wk == wl && k < lane);
             }
             ord[rank] = lane;
@@ -158,7 +171,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
 #undef BM
 #undef BC
     for (int i = lane; i < n; i += 32) out[i] = (i < s) ? Sc[sk(i)] : 0;
-    for (int ch = 0; ch < a.nch; ++ch) {
+    for (int ch = 0; ch < nch; ++ch) {
         const int i = ch * 32 + lane;
         const uint64_t code = (i < s) ? Sc[sk(i)] : 0;
         uint64_t mq = 0;
@@ -168,6 +181,25 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         }
         if (lane == 0) mqo[ch] = mq;
     }
+}
+
+cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
+{
+    const int ns = n_max + (n_max >> 3);
+    a.ns = ns;
+    const size_t per = (size_t)6 * ns * sizeof(uint64_t);
+    int cpb = (int)((48 * 1024) / per);
+    cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
+    const size_t shbytes = per * cpb;
+    static size_t attr_set = 0;
+    if (shbytes > 40 * 1024 && shbytes > attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(pathsel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)shbytes);
+        if (e != cudaSuccess) return e;
+        attr_set = shbytes;
+    }
+    pathsel_kernel<<<(a.C + cpb - 1) / cpb, 32 * cpb, shbytes, s>>>(a, cpb);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -180,20 +212,18 @@ cudaError_t launch_pathsel(const vp_plan* p, int C, cudaStream_t s)
     a.n = p->n_paths;
     a.nch = n_chunks(p->n_paths);
     a.d = p->d;
-    const int ns = p->n_paths + (p->n_paths >> 3);
-    const size_t per = (size_t)6 * ns * sizeof(uint64_t);
-    int cpb = (int)((48 * 1024) / per);
-    cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
-    const size_t shbytes = per * cpb;
-    static size_t attr_set = 0;
-    if (shbytes > 40 * 1024 && shbytes > attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pathsel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)shbytes);
-        if (e != cudaSuccess) return e;
-        attr_set = shbytes;
-    }
-    pathsel_kernel<<<(C + cpb - 1) / cpb, 32 * cpb, shbytes, s>>>(a, cpb);
-    return cudaGetLastError();
+    a.probs = nullptr;
+    a.ids = nullptr;
+    return run_pathsel(a, p->n_paths, s);
+}
+
+cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int count, int n_max, cudaStream_t s)
+{
+    PathArgs a = PathArgs();
+    a.C = count;
+    a.probs = probs;
+    a.ids = ids;
+    return run_pathsel(a, n_max, s);
 }
 
 }  // namespace vp

@@ -31,6 +31,11 @@ struct SearchArgs {
     int K, M, n, nch, m_qam;
     float tau, inv_tau;
     DeviceState d;
+    // batch mode (probs != null): block i works on problem ids[i] of the table;
+    // KM, NP give the shared-memory layout (the launch's largest K*M and n)
+    const BatchProblem* probs;
+    const int* ids;
+    int KM, NP;
 };
 
 // DEMAP selection: the q-th (0-based) nearest point t of {-1,0,1}+j{-1,0,1}
@@ -116,41 +121,61 @@ __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, 
     ti = npt(region4(py), cj);
 }
 
-template <int KT>
+template <int KT, bool BATCH>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int K = a.K, M = a.M, n = a.n, nch = a.nch;
     const int NW = blockDim.x >> 5;
+    const int c = blockIdx.x;
+    int K, M, n, nch, m_qam;
+    float tau, inv_tau;
+    int v0, v1;
+    ChanState cs;
+    const uint8_t* sym;
+    float2* xo;
+    int8_t* lo;
+    float* go;
+    if (BATCH) {
+        const BatchProblem& p = a.probs[a.ids[c]];
+        K = p.K; M = p.M; n = p.n; nch = n_chunks(p.n); m_qam = p.m_qam;
+        tau = p.tau; inv_tau = 1.0f / p.tau;
+        v0 = 0; v1 = p.S;
+        cs = chan_state(p);
+        sym = p.sym; xo = p.x; lo = p.l; go = p.gamma;
+        if (threadIdx.x == 0 && p.status) p.status[0] = p.st[0];
+    } else {
+        K = a.K; M = a.M; n = a.n; nch = a.nch; m_qam = a.m_qam;
+        tau = a.tau; inv_tau = a.inv_tau;
+        if (a.off) {
+            v0 = min(max(a.off[c], 0), a.n_vec);
+            v1 = min(max(a.off[c + 1], v0), a.n_vec);
+        } else {
+            v0 = c * a.S;
+            v1 = v0 + a.S;
+        }
+        cs = chan_state(a.d, (size_t)c, K, M, n);
+        sym = a.sym; xo = a.x; lo = a.l; go = a.gamma;
+    }
+    const int KM = BATCH ? a.KM : K * M, NP = BATCH ? a.NP : n;
     float4* utp = reinterpret_cast<float4*>(smraw);                 // [KT][KT]
     float2* utc = reinterpret_cast<float2*>(utp + KT * KT);        // [KT][KT]
     float2* pt = utc + KT * KT;                                    // [K][M] leading part of P^T
-    float2* ptl = pt + K * M;                                      // [K][M] trailing part
-    float2* bvec = ptl + K * M;                                    // [NW][KT]
+    float2* ptl = pt + KM;                                         // [K][M] trailing part
+    float2* bvec = ptl + KM;                                       // [NW][KT]
     uint64_t* paths = reinterpret_cast<uint64_t*>(bvec + NW * KT); // [n]
-    uint64_t* maxq = paths + n;                                    // [nch]
-    float* wv = reinterpret_cast<float*>(maxq + nch);              // [KT]
+    uint64_t* maxq = paths + NP;                                   // [nch]
+    float* wv = reinterpret_cast<float*>(maxq + n_chunks(NP));     // [KT]
     int* ulv = reinterpret_cast<int*>(wv + KT);                    // [KT]
-
-    const int c = blockIdx.x;
-    int v0, v1;
-    if (a.off) {
-        v0 = min(max(a.off[c], 0), a.n_vec);
-        v1 = min(max(a.off[c + 1], v0), a.n_vec);
-    } else {
-        v0 = c * a.S;
-        v1 = v0 + a.S;
-    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    if (a.d.st[c] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
+    if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
         for (int v = v0 + warp; v < v1; v += NW) {
-            if (lane < M) a.x[(size_t)v * M + lane] = make_float2(0.f, 0.f);
+            if (lane < M) xo[(size_t)v * M + lane] = make_float2(0.f, 0.f);
             if (lane < K) {
-                a.l[((size_t)v * K + lane) * 2] = 0;
-                a.l[((size_t)v * K + lane) * 2 + 1] = 0;
+                lo[((size_t)v * K + lane) * 2] = 0;
+                lo[((size_t)v * K + lane) * 2 + 1] = 0;
             }
-            if (lane == 0) a.gamma[v] = 0.f;
+            if (lane == 0) go[v] = 0.f;
         }
         return;
     }
@@ -158,27 +183,26 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
         const int r = i / KT, q = i % KT;
         const bool in = r < K && q < K;
-        utp[i] = in ? a.d.utp[((size_t)c * K + r) * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        utc[i] = in ? a.d.utc[((size_t)c * K + r) * K + q] : make_float2(0.f, 0.f);
+        utp[i] = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        utc[i] = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
     }
     for (int i = threadIdx.x; i < K * M; i += blockDim.x) {
-        pt[i] = a.d.pt[(size_t)c * K * M + i];
-        ptl[i] = a.d.ptlo[(size_t)c * K * M + i];
+        pt[i] = cs.pt[i];
+        ptl[i] = cs.ptlo[i];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) paths[i] = a.d.paths[(size_t)c * n + i];
-    for (int i = threadIdx.x; i < nch; i += blockDim.x) maxq[i] = a.d.maxq[(size_t)c * nch + i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) paths[i] = cs.paths[i];
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) maxq[i] = cs.maxq[i];
     for (int i = threadIdx.x; i < KT; i += blockDim.x) {
-        wv[i] = i < K ? a.d.w[(size_t)c * K + i] * a.tau * a.tau : 0.f;   // w_l tau^2
-        ulv[i] = i < K ? (int)a.d.ul[(size_t)c * K + i] : 0;
+        wv[i] = i < K ? cs.w[i] * tau * tau : 0.f;   // w_l tau^2
+        ulv[i] = i < K ? (int)cs.ul[i] : 0;
     }
     __syncthreads();
 
-    const float tau = a.tau, inv_tau = a.inv_tau;
     float2* bw = bvec + warp * KT;
     for (int v = v0 + warp; v < v1; v += NW) {
         // symbols in level order (lane k <-> level k) and b_k = s_k + sum_{m>k} U~_km s_m
         float2 s = make_float2(0.f, 0.f);
-        if (lane < K) s = qam_point((int)a.sym[(size_t)v * K + ulv[lane]], a.m_qam);
+        if (lane < K) s = qam_point((int)sym[(size_t)v * K + ulv[lane]], m_qam);
         float2 b = s;
         for (int m = 1; m < K; ++m) {
             const float2 sm = make_float2(__shfl_sync(kFull, s.x, m), __shfl_sync(kFull, s.y, m));
@@ -253,8 +277,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
             const int tr = (nib & 3) - 1, ti = (nib >> 2) - 1;
             u = make_float2(s.x - (float)tr * tau, s.y - (float)ti * tau);
             const int usr = ulv[lane];
-            a.l[((size_t)v * K + usr) * 2] = (int8_t)(-tr);
-            a.l[((size_t)v * K + usr) * 2 + 1] = (int8_t)(-ti);
+            lo[((size_t)v * K + usr) * 2] = (int8_t)(-tr);
+            lo[((size_t)v * K + usr) * 2 + 1] = (int8_t)(-ti);
         }
         // y = P u with P = pt + ptl: exact products and compensated sums (u holds
         // small integers, so P u keeps ~48 bits before the final rounding)
@@ -277,8 +301,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
         const float rs = __frsqrt_rn(g);
-        if (lane < M) a.x[(size_t)v * M + lane] = make_float2(y.x * rs, y.y * rs);
-        if (lane == 0) a.gamma[v] = g;
+        if (lane < M) xo[(size_t)v * M + lane] = make_float2(y.x * rs, y.y * rs);
+        if (lane == 0) go[v] = g;
         __syncwarp(kFull);
     }
 }
@@ -287,16 +311,27 @@ template <int KT>
 cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
 {
     const int NW = threads / 32;
-    const size_t sh = sizeof(float4) * KT * KT + sizeof(float2) * KT * KT + 2 * sizeof(float2) * a.K * a.M +
-                      sizeof(float2) * NW * KT + sizeof(uint64_t) * (a.n + a.nch) + sizeof(float) * KT +
+    const int KM = a.probs ? a.KM : a.K * a.M, NP = a.probs ? a.NP : a.n;
+    const size_t sh = sizeof(float4) * KT * KT + sizeof(float2) * KT * KT + 2 * sizeof(float2) * KM +
+                      sizeof(float2) * NW * KT + sizeof(uint64_t) * (NP + n_chunks(NP)) + sizeof(float) * KT +
                       sizeof(int) * KT;
-    static size_t attr = 0;
-    if (sh > 40 * 1024 && sh > attr) {
-        cudaError_t e = cudaFuncSetAttribute(search_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e != cudaSuccess) return e;
-        attr = sh;
+    if (a.probs) {
+        static size_t attr = 0;
+        if (sh > 40 * 1024 && sh > attr) {
+            cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+            if (e != cudaSuccess) return e;
+            attr = sh;
+        }
+        search_kernel<KT, true><<<C, threads, sh, s>>>(a);
+    } else {
+        static size_t attr = 0;
+        if (sh > 40 * 1024 && sh > attr) {
+            cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+            if (e != cudaSuccess) return e;
+            attr = sh;
+        }
+        search_kernel<KT, false><<<C, threads, sh, s>>>(a);
     }
-    search_kernel<KT><<<C, threads, sh, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -324,6 +359,10 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     a.tau = p->tau;
     a.inv_tau = 1.0f / p->tau;
     a.d = p->d;
+    a.probs = nullptr;
+    a.ids = nullptr;
+    a.KM = 0;
+    a.NP = 0;
     // warps per block (<= 7, the register budget of 4 blocks per SM): a
     // divisor-friendly count of the vectors per channel
     const int per = vec_off ? (n_vec + p->C - 1) / p->C : S;
@@ -337,6 +376,29 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     if (K <= 8) return launch_kt<8>(a, p->C, threads, s);
     if (K <= 12) return launch_kt<12>(a, p->C, threads, s);
     return launch_kt<16>(a, p->C, threads, s);
+}
+
+cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int count, int KT, int km_max,
+                                int n_max, int s_max, cudaStream_t s)
+{
+    SearchArgs a = SearchArgs();
+    a.probs = probs;
+    a.ids = ids;
+    a.C = count;
+    a.KM = km_max;
+    a.NP = n_max;
+    int nw = 7;
+    if (s_max <= 7) nw = s_max < 1 ? 1 : s_max;
+    else if (s_max % 7 != 0 && s_max % 6 == 0) nw = 6;
+    const int threads = nw * 32;
+    switch (KT) {
+    case 2: return launch_kt<2>(a, count, threads, s);
+    case 4: return launch_kt<4>(a, count, threads, s);
+    case 8: return launch_kt<8>(a, count, threads, s);
+    case 12: return launch_kt<12>(a, count, threads, s);
+    case 16: return launch_kt<16>(a, count, threads, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace vp

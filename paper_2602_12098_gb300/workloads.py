@@ -222,3 +222,51 @@ def job_inputs(job: Job):
     H = channels(rng, job.subcarriers, job.K, job.M, "iid")
     sym = symbols(rng, job.subcarriers * job.symbols, job.K, job.qam)
     return H, sym
+
+
+@dataclasses.dataclass
+class PackedProblems:
+    """Problems of an uneven batch packed into flat arrays (one device copy each).
+
+    Element offsets of problem i: H_off[i] (complex64), sym_off[i] (uint8 rows
+    of K), x_off[i] (complex64), l_off[i] (int8), g_off[i] (float32).
+    """
+    K: np.ndarray
+    M: np.ndarray
+    qam: np.ndarray
+    n_paths: np.ndarray
+    S: np.ndarray
+    H: np.ndarray          # complex64 [sum K*M]
+    sym: np.ndarray        # uint8 [sum S*K]
+    H_off: np.ndarray
+    sym_off: np.ndarray
+    x_off: np.ndarray
+    l_off: np.ndarray
+    g_off: np.ndarray
+    x_size: int
+    l_size: int
+    g_size: int
+
+
+def pack_problems(problems: list) -> PackedProblems:
+    K = np.array([p.K for p in problems], dtype=np.int64)
+    M = np.array([p.M for p in problems], dtype=np.int64)
+    S = np.array([p.sym.shape[0] for p in problems], dtype=np.int64)
+
+    def offsets(sizes):
+        o = np.zeros(len(sizes) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=o[1:])
+        return o
+
+    H_off = offsets(K * M)
+    sym_off = offsets(S * K)
+    x_off = offsets(S * M)
+    l_off = offsets(S * K * 2)
+    g_off = offsets(S)
+    H = np.concatenate([p.H.reshape(-1) for p in problems]).astype(np.complex64)
+    sym = np.concatenate([p.sym.reshape(-1) for p in problems]).astype(np.uint8) if S.sum() else \
+        np.zeros(0, dtype=np.uint8)
+    return PackedProblems(K=K, M=M, qam=np.array([p.qam for p in problems]), n_paths=np.array([p.n_paths for p in problems]),
+                          S=S, H=H, sym=sym, H_off=H_off[:-1], sym_off=sym_off[:-1], x_off=x_off[:-1],
+                          l_off=l_off[:-1], g_off=g_off[:-1], x_size=int(x_off[-1]), l_size=int(l_off[-1]),
+                          g_size=int(g_off[-1]))

@@ -64,3 +64,42 @@ def test_status_strings():
     assert vp.vp_status_string(0) == "ok"
     assert "invalid" in vp.vp_status_string(1)
     assert vp.vp_status_string(99) == "unknown status"
+
+
+def _desc(K=4, M=8, qam=16, n=16, S=14, tau=0.0, ptr=256):
+    return vp.vp_problem_desc(K, M, qam, n, tau, S, ptr, ptr, ptr, ptr, ptr, 0)
+
+
+def test_batch_validation_and_grouping():
+    """Batch planning is host-only: descriptors are validated and grouped
+    into one factor launch per (K, M), one path launch per n class and one
+    search launch per K tile (+ the FP64 launch)."""
+    good = [_desc(4, 8, 16, 16), _desc(8, 16, 64, 64), _desc(12, 16, 256, 256), _desc(16, 16, 256, 1024),
+            _desc(4, 8, 256, 1024), _desc(8, 16, 16, 20, S=0)]
+    assert vp.vp_precode_batch_workspace_bytes(good) > 0
+    for bad in [_desc(K=17), _desc(K=4, M=3), _desc(qam=32), _desc(n=0), _desc(K=2, M=2, n=82),
+                _desc(n=2000), _desc(S=-1), _desc(tau=-1.0), _desc(ptr=0)]:
+        assert vp.vp_precode_batch_workspace_bytes(good + [bad]) == 0
+        with pytest.raises(vp.VPError) as e:
+            vp.vp_batch_create(good + [bad])
+        assert e.value.code == 1
+    b = vp.vp_batch_create(good)
+    try:
+        # factor: (4,8), (8,16), (12,16), (16,16); paths: n classes 16, 64, 256, 1024;
+        # search: K tiles 4, 8, 12, 16; plus the FP64 fix-up
+        assert vp.vp_batch_launch_count(b) == 4 + 4 + 4 + 1
+        ws = vp.vp_batch_workspace_bytes(b)
+        assert ws == vp.vp_precode_batch_workspace_bytes(good)
+        with pytest.raises(vp.VPError) as e:          # never bound to a workspace
+            vp.vp_batch_launch(b, stream=0)
+        assert e.value.code == 5
+        with pytest.raises(vp.VPError) as e:          # workspace too small / misaligned
+            vp.vp_batch_bind(b, 4096, ws - 1, stream=0)
+        assert e.value.code == 1
+        with pytest.raises(vp.VPError) as e:
+            vp.vp_batch_bind(b, 4100, ws, stream=0)
+        assert e.value.code == 1
+    finally:
+        vp.vp_batch_destroy(b)
+    with pytest.raises(vp.VPError):
+        vp.vp_batch_create(good, fp64_threshold=float("nan"))
