@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--subcarriers", type=int, default=None,
                     help="run a reduced slot (profiling captures); the default is the full slot")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven batched-vs-plain measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
+    ap.add_argument("--serving-slots", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -120,6 +123,28 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_batch(w, rank: int, subcarriers=None):
+    """Rank r precodes its own slot (an independent seeded draw): replicas
+    share nothing, so no collective touches the data path."""
+    from paper_2602_12098_gb300 import workloads as W
+    return W.make_batch(w, slot=rank, subcarriers=subcarriers)
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest of the ranks' values (the slowest rank's time)."""
+    if dist is None or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: int, steps: int, slowest_s: float) -> float:
+    """Units all ranks processed / the slowest rank's time (weak scaling)."""
+    return ws * units_per_rank * steps / slowest_s
+
+
 def run_reference(args):
     """FP64 CPU oracle on the host cores, bounded sample per step (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -161,19 +186,230 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, sub_channels: int = 1024) -> dict:
+def cpu_baseline(w, budget_s: float = 10.0) -> dict:
+    """The oracle on whole slots of the workload (independent draws) until
+    about budget_s seconds of wall time have been spent, all host cores."""
     from oracle import oracle as O
     from paper_2602_12098_gb300 import workloads as W
     threads = os.cpu_count() or 1
-    b = W.make_batch(w, subcarriers=min(sub_channels, w.subcarriers))
-    t0 = time.perf_counter()
-    O.precode_batch(b.H, b.sym, b.vec_off, w.qam, w.n_paths, nthreads=threads)
-    dt = time.perf_counter() - t0
-    V = b.sym.shape[0]
+    O.build()
+    V = 0
+    dt = 0.0
+    slots = 0
+    while dt < budget_s and slots < 50:
+        b = W.make_batch(w, slot=100 + slots)
+        t0 = time.perf_counter()
+        O.precode_batch(b.H, b.sym, b.vec_off, w.qam, w.n_paths, nthreads=threads)
+        dt += time.perf_counter() - t0
+        V += b.sym.shape[0]
+        slots += 1
     cores = min(threads, O.max_threads()) if O.max_threads() > 1 else 1
     return {"value": V / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{b.H.shape[0]} of {w.subcarriers} subcarriers x {w.symbols} symbols ({V} vectors), "
+            "sample": f"{slots} whole slot(s) of {w.subcarriers} subcarriers x {w.symbols} symbols ({V} vectors), "
                       f"{dt:.1f} s wall"}
+
+
+def profiled_traffic(kernel_file: str) -> dict | None:
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    sources still hash to what was profiled (else None: stale counters)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    fields = {}
+    for ln in txt.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    srcs = fields.get("sources", "").split()
+    h = hashlib.sha256()
+    try:
+        for sfile in srcs:
+            h.update(open(os.path.join(ROOT, sfile), "rb").read())
+    except OSError:
+        return None
+    if not srcs or h.hexdigest() != fields.get("sources_sha256"):
+        return None
+    try:
+        return {"bytes": float(fields["dram_bytes_per_launch"]), "file": "profiles/" + kernel_file}
+    except (KeyError, ValueError):
+        return None
+
+
+def measure_batched(dev, flush) -> dict:
+    """Uneven batch: 20,000 problems x 14 vectors, (K x M, Q, n) uniform over
+    {4x8, 8x16, 12x16, 16x16} x {16, 64, 256} x {16, 64, 256, 1024}. Three
+    ways: the grouped launches of vp_batch_launch, the same captured in a
+    CUDA graph, and the plain path (one vp_factorize + vp_precode per
+    problem, one plan per distinct shape)."""
+    import numpy as np
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    from paper_2602_12098_gb300 import workloads as W
+    stream = torch.cuda.Stream(device=dev)      # graph capture needs a non-default stream
+    probs = W.uneven_problems(20000)
+    pk = W.pack_problems(probs)
+    V = int(pk.S.sum())
+    H = torch.from_numpy(pk.H).to(dev)
+    sym = torch.from_numpy(pk.sym).to(dev)
+    x = torch.empty(pk.x_size, dtype=torch.complex64, device=dev)
+    l = torch.empty(pk.l_size, dtype=torch.int8, device=dev)
+    g = torch.empty(pk.g_size, dtype=torch.float32, device=dev)
+    descs = vp.packed_descs(pk, H, sym, x, l, g)
+    out = {"workload": "20000 problems x 14 vectors, (K x M, Q, n) uniform over {4x8, 8x16, 12x16, 16x16} x "
+                       "{16, 64, 256} x {16, 64, 256, 1024}, iid channels", "vectors": V}
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    torch.cuda.synchronize()
+    with vp.Batch(descs, stream=stream) as b:
+        for _ in range(3):
+            b.launch(stream)
+        torch.cuda.synchronize()
+        ms = timed(lambda: b.launch(stream), 10)
+        out["batched_ms"] = ms
+        out["batched_vectors_per_s"] = V / (ms / 1e3)
+        out["batched_launches"] = b.launches
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            b.launch(stream)
+        def replay():
+            with torch.cuda.stream(stream):
+                graph.replay()
+
+        for _ in range(3):
+            replay()
+        ms = timed(replay, 10)
+        out["graph_ms"] = ms
+        out["graph_vectors_per_s"] = V / (ms / 1e3)
+        del graph
+
+    plans = {}
+    for i in range(len(probs)):
+        key = (int(pk.K[i]), int(pk.M[i]), int(pk.qam[i]), int(pk.n_paths[i]))
+        if key not in plans:
+            plans[key] = vp.Plan(*key)
+    hb, sb, xb, lb, gb = H.data_ptr(), sym.data_ptr(), x.data_ptr(), l.data_ptr(), g.data_ptr()
+    calls = []
+    for i in range(len(probs)):
+        key = (int(pk.K[i]), int(pk.M[i]), int(pk.qam[i]), int(pk.n_paths[i]))
+        S = int(pk.S[i])
+        calls.append((plans[key].handle, hb + 8 * int(pk.H_off[i]), sb + int(pk.sym_off[i]), S,
+                      xb + 8 * int(pk.x_off[i]), lb + int(pk.l_off[i]), gb + 4 * int(pk.g_off[i])))
+    lib = vp.load()
+    sh = stream.cuda_stream
+
+    def plain():
+        for h, hp, sp, S, xp, lp, gp in calls:
+            if lib.vp_factorize(h, hp, 1, None, None, None, None, sh) != 0:
+                raise RuntimeError("vp_factorize failed")
+            if lib.vp_precode(h, sp, S, None, S, xp, lp, gp, sh) != 0:
+                raise RuntimeError("vp_precode failed")
+
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms = timed(plain, 2)
+    out["plain_ms"] = ms
+    out["plain_vectors_per_s"] = V / (ms / 1e3)
+    out["plain_launches"] = 4 * len(probs)
+    out["plain_host_s"] = (time.perf_counter() - t0) / 2
+    for p in plans.values():
+        p.close()
+    return out
+
+
+def measure_serving(dev, n_slots: int) -> dict:
+    """Open-loop serving: Poisson job arrivals (mean 4 per 0.5 ms slot); a job
+    is one cell's slot, 3276 subcarriers x 14 symbols, K in {4, 8, 12, 16},
+    M = 16, Q in {16, 64, 256}, n = 64, iid channels. Jobs are dispatched at
+    their arrival times round-robin over 4 streams (a plan per job type and
+    stream); latency = GPU completion - arrival, on one clock through a
+    reference event. Inputs are one draw per job type, reused by its jobs."""
+    import numpy as np
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    from paper_2602_12098_gb300 import workloads as W
+    jobs = W.poisson_jobs(n_slots)
+    nstreams = 4
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
+    types = sorted({(j.K, j.M, j.qam, j.n_paths) for j in jobs})
+    bufs = {}
+    for t in types:
+        K, M, qam, n = t
+        proto = next(j for j in jobs if (j.K, j.M, j.qam, j.n_paths) == t)
+        Hn, sn = W.job_inputs(proto)
+        C, V = Hn.shape[0], sn.shape[0]
+        bufs[t] = {"H": torch.from_numpy(Hn).to(dev), "sym": torch.from_numpy(sn).to(dev), "C": C, "V": V,
+                   "S": proto.symbols,
+                   "out": [(torch.empty((V, M), dtype=torch.complex64, device=dev),
+                            torch.empty((V, K, 2), dtype=torch.int8, device=dev),
+                            torch.empty((V,), dtype=torch.float32, device=dev)) for _ in range(nstreams)],
+                   "plans": [vp.Plan(K, M, qam, n) for _ in range(nstreams)]}
+    lib = vp.load()
+
+    def enqueue(t, k):
+        bb = bufs[t]
+        h = bb["plans"][k].handle
+        x, l, g = bb["out"][k]
+        sh = streams[k].cuda_stream
+        if lib.vp_factorize(h, bb["H"].data_ptr(), bb["C"], None, None, None, None, sh) != 0:
+            raise RuntimeError("vp_factorize failed")
+        if lib.vp_precode(h, bb["sym"].data_ptr(), bb["S"], None, bb["V"], x.data_ptr(), l.data_ptr(),
+                          g.data_ptr(), sh) != 0:
+            raise RuntimeError("vp_precode failed")
+
+    torch.cuda.synchronize()
+    for t in types:                      # allocate plan state and warm up
+        for k in range(nstreams):
+            enqueue(t, k)
+    torch.cuda.synchronize()
+    ends = [torch.cuda.Event(enable_timing=True) for _ in jobs]
+    ref = torch.cuda.Event(enable_timing=True)
+    ref.record(streams[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    late_dispatch = 0.0
+    for i, j in enumerate(jobs):
+        target = t0 + j.arrival_us * 1e-6
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+        late_dispatch = max(late_dispatch, now - target)
+        k = i % nstreams
+        t = (j.K, j.M, j.qam, j.n_paths)
+        enqueue(t, k)
+        ends[i].record(streams[k])
+    torch.cuda.synchronize()
+    lat = np.array([ref.elapsed_time(e) - j.arrival_us * 1e-3 for e, j in zip(ends, jobs)])   # ms
+    done = max(ref.elapsed_time(e) for e in ends)
+    vecs = sum(bufs[(j.K, j.M, j.qam, j.n_paths)]["V"] for j in jobs)
+    for t in types:
+        for p in bufs[t]["plans"]:
+            p.close()
+    return {"workload": f"Poisson arrivals, mean 4 jobs per 0.5 ms slot, {n_slots} slots; job = 3276 subcarriers "
+                        "x 14 symbols, K in {4,8,12,16}, M 16, Q in {16,64,256}, n 64, iid",
+            "jobs": len(jobs), "p50_job_ms": float(np.percentile(lat, 50)), "p99_job_ms": float(np.percentile(lat, 99)),
+            "deadline_ms": 0.5, "deadline_miss_frac": float(np.mean(lat > 0.5)),
+            "vectors_per_s": vecs / (done / 1e3),
+            "offered_vectors_per_s": vecs / (jobs[-1].arrival_us * 1e-6), "streams": nstreams,
+            "max_dispatch_lag_ms": 1e3 * late_dispatch}
 
 
 def run_gpu(args):
@@ -191,7 +427,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = W.WORKLOADS[args.workload]
-    b = W.make_batch(w, slot=rank, subcarriers=args.subcarriers)
+    b = replica_batch(w, rank, args.subcarriers)
     C, K, M = b.H.shape
     V = b.sym.shape[0]
     S = w.symbols
@@ -249,12 +485,8 @@ def run_gpu(args):
     step_ms = [e[0].elapsed_time(e[2]) for e in ev]
     fac_ms = [e[0].elapsed_time(e[1]) for e in ev]
     srch_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = ws * V * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = whole_job_rate(ws, V, args.steps, tot_ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -274,12 +506,8 @@ def run_gpu(args):
             t0 = time.perf_counter()
             vp.vp_run_slot_host(h, Hh, C, sh, S, xh, lh, gh, stream=stream)
             ts.append(time.perf_counter() - t0)
-        e2e_s = sum(ts)
-        if dist:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * V * n_e2e / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(sum(ts), dist, dev)
+        e2e = {"value": whole_job_rate(ws, V, n_e2e, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(b.H.nbytes + b.sym.nbytes),
                "d2h_bytes_per_step": int(V * M * 8 + V * K * 2 + V * 4),
                "p50_slot_ms": 1e3 * statistics.median(ts),
@@ -298,8 +526,12 @@ def run_gpu(args):
     flops_launch = paper_work_flops(K, M, w.n_paths) * V
     search_avg = statistics.mean(srch_ms)
     achieved = flops_launch / (search_avg / 1e3) / 1e12
+    tr = profiled_traffic("search_kernel_slot16x16.md") if args.subcarriers is None else None
     roofline = {"bound": "alu", "kernel": "search_kernel<16> (vp_precode)", "achieved": achieved,
-                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": tr["bytes"] if tr else None,
+                "traffic_basis": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, {tr['file']}"
+                                  if tr else "no ncu capture of the current search kernel sources"),
                 "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz "
                               "(max SM clock, MEASURED_PEAKS.json)",
                 "work_basis": "paper's per-vector complex-multiplication count x 8 flops"}
@@ -315,6 +547,10 @@ def run_gpu(args):
             "kernel_ms": {"vp_factorize": statistics.mean(fac_ms), "vp_precode": search_avg},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches[0], "clocks": clocks}
     plan.close()
+    if ws == 1 and not args.no_batched:
+        line["batched"] = measure_batched(dev, flush)
+    if ws == 1 and not args.no_serving:
+        line["serving"] = measure_serving(dev, args.serving_slots)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
