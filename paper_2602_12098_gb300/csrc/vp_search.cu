@@ -121,6 +121,94 @@ __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, 
     ti = npt(region4(py), cj);
 }
 
+// One level of the descent for a lane's candidate: DEMAP selection of the
+// digit's point around r'_lv, PED update, the chosen t recorded as a 4-bit
+// code, and the column update r'_m -= U~_m,lv t for m < lv.
+template <int KT>
+__device__ __forceinline__ void level_step(int lv, const float4* utp, const float* wv, uint32_t cw0, uint32_t cw1,
+                                           uint32_t mq0, uint32_t mq1, float2 (&r)[KT], float& ped, uint32_t& lc0,
+                                           uint32_t& lc1)
+{
+    const int sh = 4 * (lv & 7);
+    const int q = (int)(((lv < 8) ? cw0 : cw1) >> sh) & 15;
+    const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
+    const float cx = r[lv].x, cy = r[lv].y;
+    int tr, ti;
+    select_point(cx, cy, q, mql, tr, ti);
+    const float ftr = (float)tr, fti = (float)ti;
+    const float dx = cx - ftr, dy = cy - fti;
+    ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
+    const uint32_t dig = (uint32_t)((tr + 1) | ((ti + 1) << 2)) << sh;
+    if (lv < 8) lc0 |= dig; else lc1 |= dig;
+    if (lv > 0) {
+        const float2 c1 = make_float2(-ftr, -ftr);
+        const float2 c2 = make_float2(fti, -fti);
+#pragma unroll
+        for (int m = 0; m < KT; ++m) {
+            if (m < lv) {
+                const float4 u = utp[m * KT + lv];
+                r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
+                r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
+            }
+        }
+    }
+}
+
+__host__ __device__ inline int pow2_at_least(int x)
+{
+    int p = 32;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+__host__ __device__ inline int take16(int& o, int bytes)
+{
+    const int r = o;
+    o += (bytes + 15) & ~15;
+    return r;
+}
+
+constexpr int kMaxPrefix = 32;   // distinct top-level prefixes evaluated once per vector (one lane each)
+constexpr int kSplitMax = 3;     // at most this many top levels are shared
+
+// Shared-memory layout of one search block (byte offsets, 16-byte aligned).
+struct SearchSmem {
+    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, scrl, scrp, wv, ulv, trk, pidx, misc, total;
+};
+
+__host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW)
+{
+    SearchSmem s;
+    int o = 0;
+    const int np2 = pow2_at_least(NP);
+    s.utp = take16(o, 16 * KT * KT);
+    s.utc = take16(o, 8 * KT * KT);
+    s.pt = take16(o, 8 * KM);
+    s.ptl = take16(o, 8 * KM);
+    s.bvec = take16(o, 8 * NW * KT);
+    s.scr = take16(o, 8 * NW * KT * kMaxPrefix);
+    s.tc = take16(o, 8 * np2);
+    s.tmq = take16(o, 8 * n_chunks(NP));
+    s.pcode = take16(o, 8 * kMaxPrefix);
+    s.scrl = take16(o, 8 * NW * kMaxPrefix);
+    s.scrp = take16(o, 4 * NW * kMaxPrefix);
+    s.wv = take16(o, 4 * KT);
+    s.ulv = take16(o, 4 * KT);
+    s.trk = take16(o, 2 * np2);
+    s.pidx = take16(o, np2);
+    s.misc = take16(o, 4 * (4 + 32) + 8);
+    s.total = o;
+    return s;
+}
+
+// Per channel (block): the candidate paths are re-sorted into trie order
+// (code ascending = lexicographic from level K down) with their MoP rank kept
+// for tie-breaking. The top T <= 3 levels of the distinct prefixes
+// (<= 32 of them) are evaluated once per vector, one lane per prefix, and
+// their residuals, PED and chosen points stored in shared memory; every path
+// then continues from its prefix's state through the remaining levels. The
+// arithmetic per path is the same as a full descent, so results are
+// identical; the shared levels are the ones with the most column updates.
 template <int KT, bool BATCH>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
@@ -157,15 +245,24 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         sym = a.sym; xo = a.x; lo = a.l; go = a.gamma;
     }
     const int KM = BATCH ? a.KM : K * M, NP = BATCH ? a.NP : n;
-    float4* utp = reinterpret_cast<float4*>(smraw);                 // [KT][KT]
-    float2* utc = reinterpret_cast<float2*>(utp + KT * KT);        // [KT][KT]
-    float2* pt = utc + KT * KT;                                    // [K][M] leading part of P^T
-    float2* ptl = pt + KM;                                         // [K][M] trailing part
-    float2* bvec = ptl + KM;                                       // [NW][KT]
-    uint64_t* paths = reinterpret_cast<uint64_t*>(bvec + NW * KT); // [n]
-    uint64_t* maxq = paths + NP;                                   // [nch]
-    float* wv = reinterpret_cast<float*>(maxq + n_chunks(NP));     // [KT]
-    int* ulv = reinterpret_cast<int*>(wv + KT);                    // [KT]
+    const SearchSmem L = search_smem(KT, KM, NP, NW);
+    float4* utp = reinterpret_cast<float4*>(smraw + L.utp);        // [KT][KT]
+    float2* utc = reinterpret_cast<float2*>(smraw + L.utc);        // [KT][KT]
+    float2* pt = reinterpret_cast<float2*>(smraw + L.pt);          // [K][M] leading part of P^T
+    float2* ptl = reinterpret_cast<float2*>(smraw + L.ptl);        // [K][M] trailing part
+    float2* bvec = reinterpret_cast<float2*>(smraw + L.bvec);      // [NW][KT]
+    float2* scr_all = reinterpret_cast<float2*>(smraw + L.scr);    // [NW][KT][32] prefix residuals
+    uint64_t* tc = reinterpret_cast<uint64_t*>(smraw + L.tc);      // [np2] codes, trie order
+    uint64_t* tmq = reinterpret_cast<uint64_t*>(smraw + L.tmq);    // [nch] chunk digit maxima, trie order
+    uint64_t* pcode = reinterpret_cast<uint64_t*>(smraw + L.pcode);// [32] a code of each prefix
+    uint2* scrl_all = reinterpret_cast<uint2*>(smraw + L.scrl);    // [NW][32] prefix chosen points
+    float* scrp_all = reinterpret_cast<float*>(smraw + L.scrp);    // [NW][32] prefix PED
+    float* wv = reinterpret_cast<float*>(smraw + L.wv);            // [KT]
+    int* ulv = reinterpret_cast<int*>(smraw + L.ulv);              // [KT]
+    uint16_t* trk = reinterpret_cast<uint16_t*>(smraw + L.trk);    // [np2] MoP rank of each trie position
+    uint8_t* pidx = smraw + L.pidx;                                // [np2] prefix of each trie position
+    int* misc = reinterpret_cast<int*>(smraw + L.misc);            // counts [4], per-chunk starts [32]
+    uint64_t* amq_s = reinterpret_cast<uint64_t*>(misc + 36);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
@@ -180,6 +277,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         return;
     }
 
+    const int np2 = pow2_at_least(n);
     for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
         const int r = i / KT, q = i % KT;
         const bool in = r < K && q < K;
@@ -190,15 +288,91 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         pt[i] = cs.pt[i];
         ptl[i] = cs.ptlo[i];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) paths[i] = cs.paths[i];
-    for (int i = threadIdx.x; i < nch; i += blockDim.x) maxq[i] = cs.maxq[i];
+    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        tc[i] = i < n ? cs.paths[i] : ~0ull;
+        trk[i] = (uint16_t)i;
+    }
     for (int i = threadIdx.x; i < KT; i += blockDim.x) {
         wv[i] = i < K ? cs.w[i] * tau * tau : 0.f;   // w_l tau^2
         ulv[i] = i < K ? (int)cs.ul[i] : 0;
     }
+    if (threadIdx.x < 4) misc[threadIdx.x] = 0;
     __syncthreads();
 
+    // trie order: bitonic sort of (code, rank) by code (a channel's codes are distinct)
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (np2 >> 1); i += blockDim.x) {
+                const int ix = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                const int iy = ix + j;
+                const bool up = (ix & k) == 0;
+                const uint64_t c0 = tc[ix], c1 = tc[iy];
+                if ((c0 > c1) == up && c0 != c1) {
+                    tc[ix] = c1;
+                    tc[iy] = c0;
+                    const uint16_t t = trk[ix];
+                    trk[ix] = trk[iy];
+                    trk[iy] = t;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // shared top levels: the largest T <= 3 whose distinct prefixes fit the lanes of one pass
+    int T = 0;
+    if (K == KT && KT >= 8 && nch >= 2) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+            for (int t = 1; t <= kSplitMax; ++t) {
+                const int sh = 4 * (K - t);
+                if (i == 0 || (tc[i] >> sh) != (tc[i - 1] >> sh)) atomicAdd(&misc[t], 1);
+            }
+        }
+        __syncthreads();
+        T = kSplitMax;
+        while (T > 0 && misc[T] > kMaxPrefix) --T;
+    }
+    const int psh = 4 * (K - T);   // prefix = code >> psh (T = 0: one empty prefix)
+    for (int ch = warp; ch < nch; ch += NW) {
+        const int i = ch * 32 + lane;
+        const bool st = i < n && (i == 0 || (T > 0 && (tc[i] >> psh) != (tc[i - 1] >> psh)));
+        const unsigned bal = __ballot_sync(kFull, st);
+        if (lane == 0) misc[4 + ch] = __popc(bal);
+    }
+    __syncthreads();
+    for (int ch = warp; ch < nch; ch += NW) {
+        int base = 0;
+        for (int c2 = 0; c2 < ch; ++c2) base += misc[4 + c2];
+        const int i = ch * 32 + lane;
+        const bool st = i < n && (i == 0 || (T > 0 && (tc[i] >> psh) != (tc[i - 1] >> psh)));
+        const unsigned bal = __ballot_sync(kFull, st);
+        const int incl = base + __popc(bal & (0xffffffffu >> (31 - lane)));
+        if (i < n) pidx[i] = (uint8_t)(incl - 1);
+        if (st) pcode[incl - 1] = tc[i];
+        const uint64_t code = i < n ? tc[i] : 0ull;
+        uint64_t mq = 0;
+        for (int l = 0; l < K; ++l)
+            mq |= (uint64_t)__reduce_max_sync(kFull, (unsigned)((code >> (4 * l)) & 15u)) << (4 * l);
+        if (lane == 0) tmq[ch] = mq;
+    }
+    __syncthreads();
+    const int NPF = T > 0 ? misc[T] : 1;
+    if (warp == 0) {
+        const uint64_t code = lane < NPF ? pcode[lane] : 0ull;
+        uint64_t mq = 0;
+        for (int l = K - T; l < K; ++l)
+            mq |= (uint64_t)__reduce_max_sync(kFull, (unsigned)((code >> (4 * l)) & 15u)) << (4 * l);
+        if (lane == 0) *amq_s = mq;
+    }
+    __syncthreads();
+
+    const uint64_t amq = *amq_s;
     float2* bw = bvec + warp * KT;
+    float2* scr = scr_all + warp * KT * kMaxPrefix;
+    float* scrp = scrp_all + warp * kMaxPrefix;
+    uint2* scrl = scrl_all + warp * kMaxPrefix;
+    const int KB = K - T;   // levels evaluated per path
     for (int v = v0 + warp; v < v1; v += NW) {
         // symbols in level order (lane k <-> level k) and b_k = s_k + sum_{m>k} U~_km s_m
         float2 s = make_float2(0.f, 0.f);
@@ -216,57 +390,67 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         for (int o = 16; o >= 1; o >>= 1) g0 += __shfl_xor_sync(kFull, g0, o);
         __syncwarp(kFull);
 
-        float bp = INFINITY;
-        int bi = 0x7fffffff;
-        uint32_t blc0 = 0, blc1 = 0;
-        for (int ch = 0; ch < nch; ++ch) {
-            const int jp = ch * 32 + lane;
-            const bool vld = jp < n;
-            const uint64_t code = vld ? paths[jp] : 0ull;
+        // shared top levels, one lane per prefix (T = 0: lane 0 stores the root state)
+        {
+            const uint64_t code = lane < NPF ? pcode[lane] : 0ull;
             const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
-            const uint64_t mq = maxq[ch];
-            const uint32_t mq0 = (uint32_t)mq, mq1 = (uint32_t)(mq >> 32);
             float2 r[KT];
 #pragma unroll
             for (int m = 0; m < KT; ++m) r[m] = bw[m];
             float ped = 0.f;
             uint32_t lc0 = 0, lc1 = 0;
+            constexpr int kLo = KT >= 8 ? KT - kSplitMax : KT;   // no shared levels for small tiles
+#pragma unroll
+            for (int lv = KT - 1; lv >= kLo; --lv) {
+                if (lv >= KT - T)
+                    level_step<KT>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), r, ped, lc0, lc1);
+            }
+            if (lane < NPF) {
+#pragma unroll
+                for (int m = 0; m < KT; ++m)
+                    if (m < KB) scr[m * kMaxPrefix + lane] = r[m];
+                scrp[lane] = ped;
+                scrl[lane] = make_uint2(lc0, lc1);
+            }
+        }
+        __syncwarp(kFull);
+
+        float bp = INFINITY;
+        int brk = 0x7fffffff;
+        uint32_t blc0 = 0, blc1 = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int jp = ch * 32 + lane;
+            const bool vld = jp < n;
+            const uint64_t code = vld ? tc[jp] : 0ull;
+            const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
+            const int rk = vld ? (int)trk[jp] : 0x7fffffff;
+            const int p = vld ? (int)pidx[jp] : 0;
+            const uint64_t mq = tmq[ch];
+            float2 r[KT];
+#pragma unroll
+            for (int m = 0; m < KT; ++m) r[m] = (m < KB) ? scr[m * kMaxPrefix + p] : make_float2(0.f, 0.f);
+            float ped = scrp[p];
+            const uint2 lcp = scrl[p];
+            uint32_t lc0 = lcp.x, lc1 = lcp.y;
 #pragma unroll
             for (int lv = KT - 1; lv >= 0; --lv) {
-                if (lv < K) {
-                    const int sh = 4 * (lv & 7);
-                    const int q = (int)(((lv < 8) ? cw0 : cw1) >> sh) & 15;
-                    const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
-                    const float cx = r[lv].x, cy = r[lv].y;
-                    int tr, ti;
-                    select_point(cx, cy, q, mql, tr, ti);
-                    const float ftr = (float)tr, fti = (float)ti;
-                    const float dx = cx - ftr, dy = cy - fti;
-                    ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
-                    const uint32_t dig = (uint32_t)((tr + 1) | ((ti + 1) << 2)) << sh;
-                    if (lv < 8) lc0 |= dig; else lc1 |= dig;
-                    if (lv > 0) {
-                        const float2 c1 = make_float2(-ftr, -ftr);
-                        const float2 c2 = make_float2(fti, -fti);
-#pragma unroll
-                        for (int m = 0; m < lv; ++m) {
-                            const float4 u = utp[m * KT + lv];
-                            r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
-                            r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
-                        }
-                    }
-                }
+                if (lv < KB)
+                    level_step<KT>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), r, ped, lc0, lc1);
             }
-            if (vld && ped < bp) { bp = ped; bi = jp + 1; blc0 = lc0; blc1 = lc1; }
+            if (vld && (ped < bp || (ped == bp && rk < brk))) { bp = ped; brk = rk; blc0 = lc0; blc1 = lc1; }
         }
+        // (PED, rank) minimum over the warp; candidate index = rank + 1
+        float wbp = bp;
+        int wbr = brk;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
-            const float obp = __shfl_xor_sync(kFull, bp, o);
-            const int obi = __shfl_xor_sync(kFull, bi, o);
-            if (obp < bp || (obp == bp && obi < bi)) { bp = obp; bi = obi; }
+            const float obp = __shfl_xor_sync(kFull, wbp, o);
+            const int obr = __shfl_xor_sync(kFull, wbr, o);
+            if (obp < wbp || (obp == wbp && obr < wbr)) { wbp = obp; wbr = obr; }
         }
-        const bool zero_wins = !(bp < g0);
-        const int src = zero_wins ? 0 : ((bi - 1) & 31);
+        const bool zero_wins = !(wbp < g0);
+        const unsigned who = __ballot_sync(kFull, bp == wbp && brk == wbr);
+        const int src = (zero_wins || who == 0u) ? 0 : (__ffs(who) - 1);
         uint32_t w0 = __shfl_sync(kFull, blc0, src), w1 = __shfl_sync(kFull, blc1, src);
         if (zero_wins) { w0 = 0x55555555u; w1 = 0x55555555u; }
 
@@ -312,9 +496,7 @@ cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
 {
     const int NW = threads / 32;
     const int KM = a.probs ? a.KM : a.K * a.M, NP = a.probs ? a.NP : a.n;
-    const size_t sh = sizeof(float4) * KT * KT + sizeof(float2) * KT * KT + 2 * sizeof(float2) * KM +
-                      sizeof(float2) * NW * KT + sizeof(uint64_t) * (NP + n_chunks(NP)) + sizeof(float) * KT +
-                      sizeof(int) * KT;
+    const size_t sh = (size_t)search_smem(KT, KM, NP, NW).total;
     if (a.probs) {
         static size_t attr = 0;
         if (sh > 40 * 1024 && sh > attr) {
