@@ -48,9 +48,9 @@ struct SearchArgs {
 // (|x|, |y| < 1/2, e.g. s/tau at the first level), where 2^-23 and 2^-25 are
 // representable shifts far below the spacing of distinct distances.
 //
-// Per axis (region r = [x > -1/2] + [x > 0] + [x > 1/2]) the points in
-// increasing distance are n_0, n_1, n_2 (kNTab), and their squared distances
-// exceed that of n_0 by 0, D1 = |1 - 2|x||, D2 = max(1 + 2|x|, 4|x|). The 9
+// Per axis the points in increasing distance are n_0, n_1, n_2, and their
+// squared distances exceed that of n_0 by 0, D1 = |1 - 2|x||,
+// D2 = max(1 + 2|x|, 4|x|). The 9
 // points form a 3x3 table of sums Dx_i + Dy_j (cell (i, j) = (n_i(x), n_j(y))).
 // Against the origin cell the 8 others are
 //   A=(1,0): D1x  B=(0,1): D1y  C=(2,0): D2x  D=(0,2): D2y  E=(1,1): D1x+D1y
@@ -60,11 +60,6 @@ struct SearchArgs {
 // so the rank of each cell is a short sum of these bits.
 constexpr float kEpsX = 0x1p-23f;
 constexpr float kEpsY = 0x1p-25f;
-// (n_i(r) + 1) in 2 bits at bit 2(3r + i): r0 (-1,0,1), r1 (0,-1,1), r2 (0,1,-1), r3 (1,0,-1)
-constexpr uint32_t kNTab = 0x189864u;
-
-__device__ __forceinline__ int region4(float x) { return (x > -0.5f) + (x > 0.f) + (x > 0.5f); }
-__device__ __forceinline__ int npt(int r, int i) { return (int)((kNTab >> (2 * (3 * r + i))) & 3u) - 1; }
 __device__ __forceinline__ float gap1(float x) { return fabsf(fmaf(-2.f, fabsf(x), 1.f)); }
 __device__ __forceinline__ float gap2(float x) { return fmaxf(fmaf(2.f, fabsf(x), 1.f), 4.f * fabsf(x)); }
 
@@ -88,37 +83,42 @@ __device__ __forceinline__ void rank_cell(float D1x, float D2x, float D1y, float
 }
 
 // t for rank q at effective point (cx, cy); `mq` = the warp's largest q at this
-// level (uniform) picks the cheapest branch that is exact for every lane.
+// level (uniform) picks the cheapest branch that is exact for every lane. The
+// branches only choose the cell (ci, cj). Per axis the points in increasing
+// distance are n0 (the clamped rounding), s - n0 and -s, s = +1 for x > 0
+// else -1 (the three points of {-1, 0, 1} sum to zero).
 __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, int& tr, int& ti)
 {
     const float px = cx - kEpsX, py = cy - kEpsY;
+    const int n0x = (px > 0.5f) - (px <= -0.5f);
+    const int n0y = (py > 0.5f) - (py <= -0.5f);
     if (mq == 0) {
-        tr = (px > 0.5f) - (px <= -0.5f);
-        ti = (py > 0.5f) - (py <= -0.5f);
+        tr = n0x;
+        ti = n0y;
         return;
     }
-    if (mq == 1) {                                                    // rank 0 or 1: round, or step to A or B
-        const bool f0 = gap1(px) < gap1(py);
-        const int ci = (q == 1 && f0) ? 1 : 0, cj = (q == 1 && !f0) ? 1 : 0;
-        tr = npt(region4(px), ci);
-        ti = npt(region4(py), cj);
-        return;
-    }
-    const float D1x = gap1(px), D2x = gap2(px), D1y = gap1(py), D2y = gap2(py);
+    const float D1x = gap1(px), D1y = gap1(py);
+    const bool f0 = D1x < D1y;                                        // rank 1: A (step in x) or B
     int ci, cj;
-    if (mq == 2) {
-        const bool f0 = D1x < D1y;                                    // rank 1: A or B
-        const bool g = f0 ? (D1y < D2x) : (D1x < D2y);                // rank 2: the other, or C / D
-        const int c2i = f0 ? (g ? 0 : 2) : (g ? 1 : 0);
-        const int c2j = f0 ? (g ? 1 : 0) : (g ? 0 : 2);
-        ci = q == 0 ? 0 : (q == 1 ? (f0 ? 1 : 0) : c2i);
-        cj = q == 0 ? 0 : (q == 1 ? (f0 ? 0 : 1) : c2j);
+    if (mq == 1) {
+        ci = (q == 1 && f0) ? 1 : 0;
+        cj = (q == 1 && !f0) ? 1 : 0;
     } else {
-        rank_cell(D1x, D2x, D1y, D2y, q, ci, cj);
-        if (q == 0) { ci = 0; cj = 0; }
+        const float D2x = gap2(px), D2y = gap2(py);
+        if (mq == 2) {
+            const bool g = f0 ? (D1y < D2x) : (D1x < D2y);            // rank 2: the other of A/B, or C / D
+            const int c2i = f0 ? (g ? 0 : 2) : (g ? 1 : 0);
+            const int c2j = f0 ? (g ? 1 : 0) : (g ? 0 : 2);
+            ci = q == 0 ? 0 : (q == 1 ? (f0 ? 1 : 0) : c2i);
+            cj = q == 0 ? 0 : (q == 1 ? (f0 ? 0 : 1) : c2j);
+        } else {
+            rank_cell(D1x, D2x, D1y, D2y, q, ci, cj);
+            if (q == 0) { ci = 0; cj = 0; }
+        }
     }
-    tr = npt(region4(px), ci);
-    ti = npt(region4(py), cj);
+    const int sx = px > 0.f ? 1 : -1, sy = py > 0.f ? 1 : -1;
+    tr = ci == 0 ? n0x : (ci == 1 ? sx - n0x : -sx);
+    ti = cj == 0 ? n0y : (cj == 1 ? sy - n0y : -sy);
 }
 
 // One level of the descent for a lane's candidate: DEMAP selection of the
@@ -168,12 +168,45 @@ __host__ __device__ inline int take16(int& o, int bytes)
     return r;
 }
 
+// Ascending bitonic sort of key[0..np2) (np2 a power of two, keys distinct
+// except the padding) carrying val; every thread of the block calls it.
+__device__ void block_sort(uint64_t* key, uint32_t* val, int np2)
+{
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (np2 >> 1); i += blockDim.x) {
+                const int ix = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                const int iy = ix + j;
+                const bool up = (ix & k) == 0;
+                const uint64_t c0 = key[ix], c1 = key[iy];
+                if ((c0 > c1) == up && c0 != c1) {
+                    key[ix] = c1;
+                    key[iy] = c0;
+                    const uint32_t t = val[ix];
+                    val[ix] = val[iy];
+                    val[iy] = t;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The K 4-bit digits of a path code in reverse level order (an involution).
+__device__ __forceinline__ uint64_t nibble_reverse(uint64_t c, int K)
+{
+    c = __brevll(c);                                                        // bits reversed
+    c = ((c >> 1) & 0x5555555555555555ull) | ((c & 0x5555555555555555ull) << 1);
+    c = ((c >> 2) & 0x3333333333333333ull) | ((c & 0x3333333333333333ull) << 2);   // nibbles restored
+    return K == 16 ? c : c >> (64 - 4 * K);
+}
+
 constexpr int kMaxPrefix = 32;   // distinct top-level prefixes evaluated once per vector (one lane each)
 constexpr int kSplitMax = 3;     // at most this many top levels are shared
 
 // Shared-memory layout of one search block (byte offsets, 16-byte aligned).
 struct SearchSmem {
-    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, scrl, scrp, wv, ulv, trk, pidx, misc, total;
+    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, scrl, scrp, wv, ulv, meta, misc, total;
 };
 
 __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW)
@@ -194,8 +227,7 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
     s.scrp = take16(o, 4 * NW * kMaxPrefix);
     s.wv = take16(o, 4 * KT);
     s.ulv = take16(o, 4 * KT);
-    s.trk = take16(o, 2 * np2);
-    s.pidx = take16(o, np2);
+    s.meta = take16(o, 4 * np2);
     s.misc = take16(o, 4 * (4 + 32) + 8);
     s.total = o;
     return s;
@@ -259,8 +291,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     float* scrp_all = reinterpret_cast<float*>(smraw + L.scrp);    // [NW][32] prefix PED
     float* wv = reinterpret_cast<float*>(smraw + L.wv);            // [KT]
     int* ulv = reinterpret_cast<int*>(smraw + L.ulv);              // [KT]
-    uint16_t* trk = reinterpret_cast<uint16_t*>(smraw + L.trk);    // [np2] MoP rank of each trie position
-    uint8_t* pidx = smraw + L.pidx;                                // [np2] prefix of each trie position
+    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + L.meta);  // [np2] MoP rank | prefix << 16
     int* misc = reinterpret_cast<int*>(smraw + L.misc);            // counts [4], per-chunk starts [32]
     uint64_t* amq_s = reinterpret_cast<uint64_t*>(misc + 36);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -290,7 +321,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     }
     for (int i = threadIdx.x; i < np2; i += blockDim.x) {
         tc[i] = i < n ? cs.paths[i] : ~0ull;
-        trk[i] = (uint16_t)i;
+        meta[i] = (uint32_t)i;
     }
     for (int i = threadIdx.x; i < KT; i += blockDim.x) {
         wv[i] = i < K ? cs.w[i] * tau * tau : 0.f;   // w_l tau^2
@@ -299,25 +330,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     if (threadIdx.x < 4) misc[threadIdx.x] = 0;
     __syncthreads();
 
-    // trie order: bitonic sort of (code, rank) by code (a channel's codes are distinct)
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < (np2 >> 1); i += blockDim.x) {
-                const int ix = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-                const int iy = ix + j;
-                const bool up = (ix & k) == 0;
-                const uint64_t c0 = tc[ix], c1 = tc[iy];
-                if ((c0 > c1) == up && c0 != c1) {
-                    tc[ix] = c1;
-                    tc[iy] = c0;
-                    const uint16_t t = trk[ix];
-                    trk[ix] = trk[iy];
-                    trk[iy] = t;
-                }
-            }
-            __syncthreads();
-        }
-    }
+    // trie order (code ascending: lexicographic from level K down) to find the prefixes
+    block_sort(tc, meta, np2);
 
     // shared top levels: the largest T <= 3 whose distinct prefixes fit the lanes of one pass
     int T = 0;
@@ -348,8 +362,19 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         const bool st = i < n && (i == 0 || (T > 0 && (tc[i] >> psh) != (tc[i - 1] >> psh)));
         const unsigned bal = __ballot_sync(kFull, st);
         const int incl = base + __popc(bal & (0xffffffffu >> (31 - lane)));
-        if (i < n) pidx[i] = (uint8_t)(incl - 1);
+        if (i < n) meta[i] |= (uint32_t)(incl - 1) << 16;
         if (st) pcode[incl - 1] = tc[i];
+    }
+    __syncthreads();
+    // evaluation order: level 1 most significant (the light levels, where the
+    // candidates' digits differ most), so a 32-path chunk shares small digits
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tc[i] = nibble_reverse(tc[i], K);
+    __syncthreads();
+    block_sort(tc, meta, np2);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tc[i] = nibble_reverse(tc[i], K);
+    __syncthreads();
+    for (int ch = warp; ch < nch; ch += NW) {
+        const int i = ch * 32 + lane;
         const uint64_t code = i < n ? tc[i] : 0ull;
         uint64_t mq = 0;
         for (int l = 0; l < K; ++l)
@@ -423,8 +448,9 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
             const bool vld = jp < n;
             const uint64_t code = vld ? tc[jp] : 0ull;
             const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
-            const int rk = vld ? (int)trk[jp] : 0x7fffffff;
-            const int p = vld ? (int)pidx[jp] : 0;
+            const uint32_t mt = vld ? meta[jp] : 0u;
+            const int rk = vld ? (int)(mt & 0xffffu) : 0x7fffffff;
+            const int p = (int)(mt >> 16);
             const uint64_t mq = tmq[ch];
             float2 r[KT];
 #pragma unroll
