@@ -44,14 +44,15 @@ __device__ __forceinline__ bool key_less(uint64_t am, uint64_t ac, uint64_t bm, 
 }
 
 // First `nout` outputs of the merge of sorted A[0..na) with the sorted list
-// B[0..nb) shifted by (dm, dc), into O; lane j writes outputs [j*per, (j+1)*per).
-// The metric decides; the code is compared only when two metrics are equal.
+// B[0..nb) shifted by (dm, dc), into O; thread t of the channel's `tpc`
+// threads writes outputs [t*per, (t+1)*per). The metric decides; the code is
+// compared only when two metrics are equal.
 __device__ void merge_shift(const uint64_t* Am, const uint64_t* Ac, int na,
                             const uint64_t* Bm, const uint64_t* Bc, int nb, uint64_t dm, uint64_t dc,
-                            uint64_t* Om, uint64_t* Oc, int nout, int lane)
+                            uint64_t* Om, uint64_t* Oc, int nout, int t, int tpc)
 {
-    const int per = (nout + 31) >> 5;
-    const int d0 = min(lane * per, nout);
+    const int per = (nout + tpc - 1) / tpc;
+    const int d0 = min(t * per, nout);
     const int d1 = min(d0 + per, nout);
     if (d0 >= d1) return;
     int lo = max(0, d0 - nb), hi = min(d0, na);
@@ -85,14 +86,18 @@ __device__ void merge_shift(const uint64_t* Am, const uint64_t* Ac, int na,
     }
 }
 
-// One warp per channel; a block holds `cpb` channels (shared memory 48 n bytes each).
+// A channel is worked on by `tpc` threads: one warp (a block then holds `cpb`
+// channels) or a whole block of 2-4 warps (cpb = 1), which shortens the
+// dependent merge chains of a channel. Shared memory: 48 n bytes per channel.
 __global__ void pathsel_kernel(PathArgs a, int cpb)
 {
     extern __shared__ uint64_t shm[];
     __shared__ uint64_t qws[8][kMaxK];
     __shared__ int ords[8][kMaxK];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ci = blockIdx.x * cpb + warp;
+    const int tpc = blockDim.x / cpb;                            // threads per channel
+    const int grp = threadIdx.x / tpc, t = threadIdx.x % tpc;
+    const int lane = threadIdx.x & 31, wig = t >> 5;             // lane, warp within the channel's group
+    const int ci = blockIdx.x * cpb + grp;
     if (ci >= a.C) return;
     int n = a.n, K = a.K, nch = a.nch;
     ChanState cs;
@@ -106,22 +111,22 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         cs = chan_state(a.d, (size_t)ci, K, 0, n);
     }
     const int ns = sk(n);                                        // skewed length of one list
-    uint64_t* base = shm + (size_t)warp * 6 * a.ns;
+    uint64_t* base = shm + (size_t)grp * 6 * a.ns;
     // buffer b (0..2): metrics at base + 2 b ns, codes at base + (2 b + 1) ns
     // (pointer arithmetic: an indexed pointer array would live in local memory)
 #define BM(b) (base + 2 * (b) * ns)
 #define BC(b) (base + (2 * (b) + 1) * ns)
-    uint64_t* qw = qws[warp];
-    int* ord = ords[warp];
+    uint64_t* qw = qws[grp];
+    int* ord = ords[grp];
     uint64_t* out = cs.paths;
     uint64_t* mqo = cs.maxq;
 
     if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
-        for (int i = lane; i < n; i += 32) out[i] = 0;
-        for (int i = lane; i < nch; i += 32) mqo[i] = 0;
+        for (int i = t; i < n; i += tpc) out[i] = 0;
+        for (int i = t; i < nch; i += tpc) mqo[i] = 0;
         return;
     }
-    {
+    if (wig == 0) {
         const float wl = lane < K ? cs.w[lane] : 0.f;
         float wmax = wl;
 #pragma unroll
@@ -140,7 +145,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         }
         if (lane == 0) { BM(0)[0] = 0; BC(0)[0] = 0; }
     }
-    __syncwarp(kFull);
+    if (tpc == 32) __syncwarp(kFull); else __syncthreads();
 
     int iS = 0, s = 1;
     for (int li = 0; li < K; ++li) {
@@ -158,8 +163,8 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
             if (skip) continue;
             const int io = (ix == iS) ? (iS + 1) % 3 : 3 - ix - iS;
             const int nout = min(nx + nb, n);
-            merge_shift(BM(ix), BC(ix), nx, BM(ib), BC(ib), nb, dm, dc, BM(io), BC(io), nout, lane);
-            __syncwarp(kFull);
+            merge_shift(BM(ix), BC(ix), nx, BM(ib), BC(ib), nb, dm, dc, BM(io), BC(io), nout, t, tpc);
+            if (tpc == 32) __syncwarp(kFull); else __syncthreads();
             ix = io;
             nx = nout;
         }
@@ -170,8 +175,8 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
     const uint64_t* Sc = BC(iS);
 #undef BM
 #undef BC
-    for (int i = lane; i < n; i += 32) out[i] = (i < s) ? Sc[sk(i)] : 0;
-    for (int ch = 0; ch < nch; ++ch) {
+    for (int i = t; i < n; i += tpc) out[i] = (i < s) ? Sc[sk(i)] : 0;
+    for (int ch = wig; ch < nch; ch += tpc >> 5) {
         const int i = ch * 32 + lane;
         const uint64_t code = (i < s) ? Sc[sk(i)] : 0;
         uint64_t mq = 0;
@@ -188,8 +193,13 @@ cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
     const int ns = n_max + (n_max >> 3);
     a.ns = ns;
     const size_t per = (size_t)6 * ns * sizeof(uint64_t);
-    int cpb = (int)((48 * 1024) / per);
-    cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
+    // long lists: a block of warps per channel; short ones: a warp per channel
+    const int tpc = n_max >= 128 ? 64 : 32;
+    int cpb = 1;
+    if (tpc == 32) {
+        cpb = (int)((48 * 1024) / per);
+        cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
+    }
     const size_t shbytes = per * cpb;
     static size_t attr_set = 0;
     if (shbytes > 40 * 1024 && shbytes > attr_set) {
@@ -198,7 +208,7 @@ cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = shbytes;
     }
-    pathsel_kernel<<<(a.C + cpb - 1) / cpb, 32 * cpb, shbytes, s>>>(a, cpb);
+    pathsel_kernel<<<(a.C + cpb - 1) / cpb, tpc * cpb, shbytes, s>>>(a, cpb);
     return cudaGetLastError();
 }
 
