@@ -284,8 +284,10 @@ void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int M
 }
 
 /* ------------------------------------------------------------------------ */
-/* Whole pipeline over channels x vectors (Alg. 2 end to end, lambda = 0). */
-static void precode_channel(int K, int M, int qam, double tau, int n_paths,
+/* Whole pipeline over channels x vectors (Alg. 2 end to end). lambda > 0 is
+ * the Tikhonov-regularised form: Hbar = [H lambda*I], Qbar has M+K columns,
+ * and x is the first M entries of w / sqrt(gamma) with gamma = ||w||^2. */
+static void precode_channel(int K, int M, int qam, double tau, double lambda, int n_paths,
                             const float* Hc, int v0, int v1, const uint8_t* sym_idx,
                             double* x, int8_t* l, double* gamma, int32_t* best, uint8_t* status)
 {
@@ -301,7 +303,7 @@ static void precode_channel(int K, int M, int qam, double tau, int n_paths,
     uint64_t* codes = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_paths);
 
     for (int i = 0; i < 2 * K * M; i++) H[i] = (double)Hc[i];
-    int rc = orc_isrqd(K, M, H, 0.0, ul, R, Q);
+    int rc = orc_isrqd(K, M, H, lambda, ul, R, Q);
     *status = (uint8_t)rc;
     int np = 0;
     if (rc == 0) {
@@ -335,18 +337,19 @@ static void precode_channel(int K, int M, int qam, double tau, int n_paths,
     free(H); free(R); free(Rt); free(Q); free(wgt); free(v); free(ul); free(t); free(codes);
 }
 
-int orc_precode_batch(int K, int M, int qam, double tau, int n_paths, int C,
+int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int n_paths, int C,
                       const float* H, const int32_t* vec_off, const uint8_t* sym_idx,
                       double* x, int8_t* l, double* gamma, int32_t* best,
                       uint8_t* status, int nthreads)
 {
-    if (K < 1 || K > 16 || M < K || n_paths < 1 || C < 0) return -1;
+    if (K < 1 || K > 16 || M < 1 || n_paths < 1 || C < 0 || !(lambda >= 0.0)) return -1;
+    if (M < K && lambda == 0.0) return -1;   /* H H^H is singular without the regularisation */
     if (nthreads < 1) nthreads = 1;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (int c = 0; c < C; c++)
-        precode_channel(K, M, qam, tau, n_paths, H + (size_t)c * 2 * K * M,
+        precode_channel(K, M, qam, tau, lambda, n_paths, H + (size_t)c * 2 * K * M,
                         vec_off[c], vec_off[c + 1], sym_idx, x, l, gamma, best, &status[c]);
     return 0;
 }

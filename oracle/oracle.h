@@ -94,6 +94,10 @@ void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int M
                        int* t_level, double* gamma, double* x, int* best, double* d_all);
 
 /* Whole pipeline over a batch of channels, as the GPU library computes it.
+ *   lambda     Tikhonov parameter of Alg. 2 "Regularize & factorize"
+ *              (0: the plain sorted RQ, needs M >= K); with lambda > 0,
+ *              gamma = ||w||^2 over all M+K entries of w = Qbar^H Rt (v - tau t)
+ *              and x = the first M entries of w / sqrt(gamma)
  *   H          complex64 [C][K][M] as float pairs (the GPU's own input)
  *   vec_off    [C+1] vector ranges per channel (channel c owns vectors
  *              vec_off[c] .. vec_off[c+1]-1)
@@ -102,7 +106,7 @@ void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int M
  * in user order, gamma [V], best [V]; per channel: status [C].
  * Channels whose status is nonzero get zero outputs.
  * nthreads > 1 runs channels in parallel (OpenMP), when built with it. */
-int orc_precode_batch(int K, int M, int qam, double tau, int n_paths, int C,
+int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int n_paths, int C,
                       const float* H, const int32_t* vec_off, const uint8_t* sym_idx,
                       double* x, int8_t* l, double* gamma, int32_t* best,
                       uint8_t* status, int nthreads);

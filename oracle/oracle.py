@@ -65,7 +65,7 @@ def lib():
             L.orc_search_vector.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp,
                                             ctypes.c_double, ctypes.c_int, u64p, ip, dp, dp, ip, dp]
             L.orc_precode_batch.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                             ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 8
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 8
                                             + [ctypes.c_int])
             L.orc_precode_batch.restype = ctypes.c_int
             L.orc_brute_min.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ip]
@@ -197,12 +197,12 @@ def max_threads() -> int:
 # --------------------------------------------------------------------------
 # Per-channel factor bundle and the whole pipeline.
 
-def factor_channel(H, n_paths: int):
-    """Alg. 2 pre-processing of one channel (lambda = 0).
+def factor_channel(H, n_paths: int, lam: float = 0.0):
+    """Alg. 2 pre-processing of one channel (Regularize & factorize, MoP paths).
 
     Returns dict(status, user_of_level, R, Rt (= U), Qbar, w, codes, metric).
     """
-    rc, ul, R, Q = isrqd(H, 0.0)
+    rc, ul, R, Q = isrqd(H, lam)
     out = {"status": rc, "user_of_level": ul, "R": R, "Qbar": Q}
     if rc != 0:
         return out
@@ -214,7 +214,7 @@ def factor_channel(H, n_paths: int):
 
 
 def precode_batch(H, sym_idx, vec_off, qam: int, n_paths: int, tau: float | None = None,
-                  nthreads: int = 1):
+                  nthreads: int = 1, lam: float = 0.0):
     """Whole pipeline (factor + MoP + search + x) over channels.
 
     H        complex64 [C, K, M]
@@ -234,7 +234,7 @@ def precode_batch(H, sym_idx, vec_off, qam: int, n_paths: int, tau: float | None
     gamma = np.zeros(V, dtype=np.float64)
     best = np.zeros(V, dtype=np.int32)
     status = np.zeros(C, dtype=np.uint8)
-    rc = lib().orc_precode_batch(K, M, qam, tau, int(n_paths), C,
+    rc = lib().orc_precode_batch(K, M, qam, tau, float(lam), int(n_paths), C,
                                  H.ctypes.data, vec_off.ctypes.data, sym_idx.ctypes.data,
                                  x.ctypes.data, l.ctypes.data, gamma.ctypes.data,
                                  best.ctypes.data, status.ctypes.data, int(nthreads))
