@@ -76,7 +76,8 @@ typedef enum {
 /*
  * Create a plan for one problem shape.
  *   K        users, 1 <= K <= VP_MAX_K
- *   M        antennas, K <= M <= VP_MAX_M (lambda = 0 needs H H^H invertible)
+ *   M        antennas, 1 <= M <= VP_MAX_M; K > M (overloaded) needs lambda > 0
+ *            (vp_plan_set_lambda) before vp_factorize
  *   qam      4, 16, 64 or 256; QAM index i maps to the odd-integer point
  *            (2(i mod m) - (m-1)) + j(2 floor(i/m) - (m-1)), m = sqrt(qam)
  *   n_paths  candidate paths, 1 <= n_paths <= min(9^K, VP_MAX_PATHS)
@@ -95,6 +96,19 @@ vp_status vp_plan_create(int K, int M, int qam, int n_paths, float tau, vp_plan*
  * U). 0 sends every channel to FP64; +inf none. Negative or NaN is invalid. */
 vp_status vp_plan_set_fp64_threshold(vp_plan* plan, float kappa_hat);
 
+/*
+ * Tikhonov regularisation of Alg. 2 "Regularize & factorize": the factor is
+ * the sorted RQ of Hbar = [H  lambda*I] (Section III-A-1), so
+ * (H H^H + lambda^2 I)^-1 = U^H U and P = H^H (H H^H + lambda^2 I)^-1 (RZF).
+ * The paper takes lambda = sigma / E|s_l| (noise standard deviation over the
+ * mean symbol magnitude). With lambda > 0, gamma = ||w||^2 over all M + K
+ * entries of Alg. 2's w = Qbar^H U (s + tau l) and x is its first M entries
+ * over sqrt(gamma), so ||x|| < 1. 0 (the default) is the plain sorted RQ.
+ * Negative or non-finite is invalid. Resident channels are dropped: call
+ * vp_factorize again. (The uneven-batch entry points use lambda = 0.)
+ */
+vp_status vp_plan_set_lambda(vp_plan* plan, float lambda);
+
 /* Free the plan and its device state. Synchronises the device first so that
  * no enqueued work still reads the state. NULL is accepted. */
 vp_status vp_plan_destroy(vp_plan* plan);
@@ -108,10 +122,12 @@ vp_status vp_plan_destroy(vp_plan* plan);
  *   U       optional (may be NULL): complex64 [C][K][K], the upper factor
  *           U = R^-1 in LEVEL order ((H_perm H_perm^H)^-1 = U^H U)
  *   P       optional (may be NULL): complex64 [C][M][K], the precoding
- *           matrix P = H^H (H H^H)^-1 in USER order (x = P u / sqrt(gamma))
+ *           matrix P = H^H (H H^H + lambda^2 I)^-1 in USER order
+ *           (x = P u / sqrt(gamma))
  *   user_of_level  optional (may be NULL): uint8 [C][K], the user at each level
  *   status  optional (may be NULL): uint8 [C], VP_CH_* bits per channel
  * Growing the plan allocates device memory (cudaMalloc) and synchronises.
+ * Returns VP_ERR_INVALID_ARG for K > M with lambda = 0.
  */
 vp_status vp_factorize(vp_plan* plan, const void* H, int C, void* U, void* P,
                        uint8_t* user_of_level, uint8_t* status, void* stream);
@@ -125,9 +141,9 @@ vp_status vp_factorize(vp_plan* plan, const void* H, int C, void* U, void* P,
  *                vec_offsets[c] .. vec_offsets[c+1]-1 (non-decreasing,
  *                vec_offsets[0] = 0); then S is ignored and V = n_vec
  *   n_vec        number of vectors V (must equal C*S when vec_offsets is NULL)
- *   x            complex64 [V][M] precoded vectors, ||x|| = 1
+ *   x            complex64 [V][M] precoded vectors, ||x|| = 1 (< 1 with lambda > 0)
  *   l            int8 [V][K][2] perturbation (re, im) in USER order, entries in {-1,0,1}
- *   gamma        float [V], gamma = ||U (s + tau l)||^2 of the chosen candidate
+ *   gamma        float [V], gamma = ||U (s + tau l)||^2 = ||w||^2 of the chosen candidate
  * Returns VP_ERR_NOT_FACTORIZED if no channels are resident.
  */
 vp_status vp_precode(vp_plan* plan, const uint8_t* sym_idx, int S, const int32_t* vec_offsets,

@@ -21,8 +21,8 @@ from . import _build
 
 __all__ = [
     "VPError", "load", "build", "library_path",
-    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize", "vp_precode",
-    "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
+    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_destroy", "vp_factorize",
+    "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
     "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_problem_desc", "vp_batch_create",
     "vp_batch_workspace_bytes", "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy",
     "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
@@ -37,7 +37,8 @@ VP_MAX_M = 16
 VP_MAX_PATHS = 1024
 
 EXPORTED_SYMBOLS = (
-    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize", "vp_precode",
+    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_destroy", "vp_factorize",
+    "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
     "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_batch_create", "vp_batch_workspace_bytes",
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
@@ -83,6 +84,7 @@ def load():
             L.vp_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                          ctypes.POINTER(vpp)]
             L.vp_plan_set_fp64_threshold.argtypes = [vpp, ctypes.c_float]
+            L.vp_plan_set_lambda.argtypes = [vpp, ctypes.c_float]
             L.vp_plan_destroy.argtypes = [vpp]
             L.vp_factorize.argtypes = [vpp, vpp, ctypes.c_int, vpp, vpp, vpp, vpp, vpp]
             L.vp_precode.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp]
@@ -107,7 +109,8 @@ def load():
             L.vp_precode_batch_workspace_bytes.restype = ctypes.c_size_t
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
-            for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_destroy", "vp_factorize",
+            for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_destroy",
+                         "vp_factorize",
                          "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_precode_noalloc", "vp_batch_create",
                          "vp_batch_bind", "vp_batch_launch", "vp_batch_destroy", "vp_precode_batch"):
                 getattr(L, name).restype = ctypes.c_int
@@ -159,6 +162,10 @@ def vp_plan_create(K: int, M: int, qam: int, n_paths: int, tau: float = 0.0) -> 
 
 def vp_plan_set_fp64_threshold(plan: int, kappa_hat: float) -> None:
     _check(load().vp_plan_set_fp64_threshold(plan, float(kappa_hat)), "vp_plan_set_fp64_threshold")
+
+
+def vp_plan_set_lambda(plan: int, lam: float) -> None:
+    _check(load().vp_plan_set_lambda(plan, float(lam)), "vp_plan_set_lambda")
 
 
 def vp_plan_destroy(plan: int) -> None:
@@ -309,11 +316,13 @@ class Plan:
     """Owning handle of a vp_plan (destroys it on close / exit of a with-block)."""
 
     def __init__(self, K: int, M: int, qam: int, n_paths: int, tau: float = 0.0,
-                 fp64_threshold: float | None = None):
+                 fp64_threshold: float | None = None, lam: float = 0.0):
         self.K, self.M, self.qam, self.n_paths = K, M, qam, n_paths
         self.handle = vp_plan_create(K, M, qam, n_paths, tau)
         if fp64_threshold is not None:
             vp_plan_set_fp64_threshold(self.handle, fp64_threshold)
+        if lam:
+            vp_plan_set_lambda(self.handle, lam)
 
     def close(self):
         if self.handle:

@@ -40,11 +40,13 @@ bool dalloc(T** p, size_t count)
 
 vp_status ensure_capacity(vp_plan* p, int C)
 {
-    if (C <= p->cap) return VP_OK;
+    const int mp = vp::p_rows(p);
+    if (C <= p->cap && mp == p->cap_mp) return VP_OK;
     cudaDeviceSynchronize();                 // no enqueued work may still read the old state
     free_state(p->d);
     p->cap = 0;
-    const size_t K = p->K, M = p->M, n = p->n_paths, nch = vp::n_chunks(p->n_paths);
+    p->cap_mp = 0;
+    const size_t K = p->K, M = (size_t)mp, n = p->n_paths, nch = vp::n_chunks(p->n_paths);
     vp::DeviceState d;
     bool ok = dalloc(&d.utp, (size_t)C * K * K) && dalloc(&d.utc, (size_t)C * K * K) &&
               dalloc(&d.w, (size_t)C * K) && dalloc(&d.ul, (size_t)C * K) && dalloc(&d.pt, (size_t)C * K * M) && dalloc(&d.ptlo, (size_t)C * K * M) &&
@@ -57,6 +59,7 @@ vp_status ensure_capacity(vp_plan* p, int C)
     }
     p->d = d;
     p->cap = C;
+    p->cap_mp = mp;
     return VP_OK;
 }
 
@@ -98,7 +101,7 @@ vp_status vp_plan_create(int K, int M, int qam, int n_paths, float tau, vp_plan*
 {
     if (!out) return VP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (K < 1 || K > VP_MAX_K || M < K || M > VP_MAX_M || !valid_qam(qam)) return VP_ERR_INVALID_ARG;
+    if (K < 1 || K > VP_MAX_K || M < 1 || M > VP_MAX_M || !valid_qam(qam)) return VP_ERR_INVALID_ARG;
     if (n_paths < 1 || n_paths > VP_MAX_PATHS || (long long)n_paths > pow9(K)) return VP_ERR_INVALID_ARG;
     if (!(tau >= 0.f) || !std::isfinite(tau)) return VP_ERR_INVALID_ARG;
     vp_plan* p = new (std::nothrow) vp_plan();
@@ -116,6 +119,14 @@ vp_status vp_plan_set_fp64_threshold(vp_plan* p, float kappa_hat)
 {
     if (!p || std::isnan(kappa_hat) || kappa_hat < 0.f) return VP_ERR_INVALID_ARG;
     p->kappa_thr = kappa_hat;
+    return VP_OK;
+}
+
+vp_status vp_plan_set_lambda(vp_plan* p, float lambda)
+{
+    if (!p || !(lambda >= 0.f) || !std::isfinite(lambda)) return VP_ERR_INVALID_ARG;
+    p->lambda = lambda;
+    p->C = 0;   // the resident state no longer matches: factorise again
     return VP_OK;
 }
 
@@ -137,6 +148,7 @@ vp_status vp_factorize(vp_plan* p, const void* H, int C, void* U, void* P, uint8
                        uint8_t* status, void* stream)
 {
     if (!p || !H || C < 1) return VP_ERR_INVALID_ARG;
+    if (p->K > p->M && !(p->lambda > 0.f)) return VP_ERR_INVALID_ARG;   // H H^H singular without lambda
     vp_status st = ensure_capacity(p, C);
     if (st != VP_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

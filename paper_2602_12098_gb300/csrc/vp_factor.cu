@@ -28,6 +28,8 @@ constexpr unsigned kFull = 0xffffffffu;
 struct FactorArgs {
     const float2* H;
     int C, K, M, n;
+    int Mp;          // rows of P kept (M, or M + K with lambda > 0)
+    float lambda;    // Tikhonov parameter (plan layout only; the batch table has lambda = 0)
     float kappa_thr;
     DeviceState d;
     float2* U_out;
@@ -63,7 +65,7 @@ __device__ __forceinline__ FChan fchan(const FactorArgs& a, int c, int K, int M)
         f.ul_out = nullptr;
     } else {
         f.H = a.H + (size_t)c * K * M;
-        f.s = chan_state(a.d, (size_t)c, K, M, a.n);
+        f.s = chan_state(a.d, (size_t)c, K, a.Mp, a.n);
         f.U_out = a.U_out ? a.U_out + (size_t)c * K * K : nullptr;
         f.P_out = a.P_out ? a.P_out + (size_t)c * M * K : nullptr;
         f.ul_out = a.ul_out ? a.ul_out + (size_t)c * K : nullptr;
@@ -83,7 +85,7 @@ struct Smem32 {
     int piv[kMaxK];            // user pivoted at step t
 };
 
-__device__ __forceinline__ void write_channel_outputs_zero(const FChan& f, int K, int M, int j)
+__device__ __forceinline__ void write_channel_outputs_zero(const FChan& f, int K, int M, int Mp, int j)
 {
     if (j < K) {
         for (int k = 0; k < K; ++k) {
@@ -91,10 +93,10 @@ __device__ __forceinline__ void write_channel_outputs_zero(const FChan& f, int K
             f.s.utc[j * K + k] = make_float2(0.f, 0.f);
             if (f.U_out) f.U_out[j * K + k] = make_float2(0.f, 0.f);
         }
-        for (int m = 0; m < M; ++m) {
-            f.s.pt[j * M + m] = make_float2(0.f, 0.f);
-            f.s.ptlo[j * M + m] = make_float2(0.f, 0.f);
-            if (f.P_out) f.P_out[m * K + j] = make_float2(0.f, 0.f);
+        for (int m = 0; m < Mp; ++m) {
+            f.s.pt[j * Mp + m] = make_float2(0.f, 0.f);
+            f.s.ptlo[j * Mp + m] = make_float2(0.f, 0.f);
+            if (f.P_out && m < M) f.P_out[m * K + j] = make_float2(0.f, 0.f);
         }
         f.s.w[j] = 0.f;
         f.s.ul[j] = (uint8_t)j;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     const unsigned hmask = 0xFFFFu << (16 * hw);
     const int ci = blockIdx.x * kChPerBlock32 + slot;
     const bool valid = ci < a.C;
-    const int K = a.K, M = a.M;
+    const int K = a.K, M = a.M, Mp = a.Mp;
     const int c = valid ? (a.ids ? a.ids[ci] : ci) : 0;   // channel (plain) or table index (batch)
     const FChan f = fchan(a, c, K, M);
     const bool act = j < K;
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
         if (valid && act && m < M) h = f.H[j * M + m];
         finite = finite && isfinite(h.x) && isfinite(h.y);
         av[m] = make_float2(h.x, -h.y);
+        if (act && m == M + j && a.lambda > 0.f) av[m] = make_float2(a.lambda, 0.f);   // Hbar = [H lambda*I]
     }
     const bool nonfinite = (__ballot_sync(kFull, !finite) & hmask) != 0u;
     if (nonfinite) {
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     if (!valid) return;
 
     if (nonfinite) {
-        write_channel_outputs_zero(f, K, M, j);
+        write_channel_outputs_zero(f, K, M, Mp, j);
         if (j == 0) f.s.st[0] = (uint8_t)VP_CH_NONFINITE;
         return;
     }
@@ -336,10 +339,10 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
         const int u = sm.piv[K - 1 - k];
 #pragma unroll
         for (int m = 0; m < MT; ++m) {
-            if (m < M) {
-                f.s.pt[u * M + m] = z[m];
-                f.s.ptlo[u * M + m] = make_float2(0.f, 0.f);
-                if (f.P_out) f.P_out[m * K + u] = z[m];
+            if (m < Mp) {
+                f.s.pt[u * Mp + m] = z[m];
+                f.s.ptlo[u * Mp + m] = make_float2(0.f, 0.f);
+                if (f.P_out && m < M) f.P_out[m * K + u] = z[m];
             }
         }
     }
@@ -405,6 +408,8 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
         const int c = a.flags[slot];
         const int K = a.probs ? a.probs[c].K : a.K;
         const int M = a.probs ? a.probs[c].M : a.M;
+        const int Mp = a.probs ? M : a.Mp;
+        const float lam = a.probs ? 0.f : a.lambda;
         const FChan f = fchan(a, c, K, M);
         for (int i = lane; i < K * M; i += 32) sm.h[i / M][i % M] = f.H[i];
         if (lane < K) sm.rem[lane] = lane;
@@ -421,7 +426,8 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 dot2_acc(x.y, y.x, im, ime);
                 dot2_acc(-x.x, y.y, im, ime);
             }
-            const double2 g = make_double2((double)re + (double)ree, (double)im + (double)ime);
+            double2 g = make_double2((double)re + (double)ree, (double)im + (double)ime);
+            if (r == q) g.x += (double)lam * (double)lam;          // H H^H + lambda^2 I
             sm.s[r][q] = g;
             sm.s[q][r] = zconj(g);
         }
@@ -577,13 +583,26 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
                 const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
                 const int uk = sm.uol[k];
-                f.s.pt[uk * M + m] = hi;
-                f.s.ptlo[uk * M + m] = lo;
+                f.s.pt[uk * Mp + m] = hi;
+                f.s.ptlo[uk * Mp + m] = lo;
                 if (f.P_out) f.P_out[m * K + uk] = hi;
+            }
+            // regularisation rows (lambda > 0): row M + u of P is lambda A[level of u][.]
+            for (int e = lane; e < (Mp - M) * K; e += 32) {
+                const int u = e / K, k = e % K;
+                int lu = 0;
+                for (int i = 0; i < K; ++i) lu = (sm.uol[i] == u) ? i : lu;
+                const float2 ah = sm.ahi[lu][k], al = sm.alo[lu][k];
+                float hx, ex, hy, ey;
+                two_prod(lam, ah.x, hx, ex);
+                two_prod(lam, ah.y, hy, ey);
+                const int uk = sm.uol[k];
+                f.s.pt[uk * Mp + M + u] = make_float2(hx, hy);
+                f.s.ptlo[uk * Mp + M + u] = make_float2(fmaf(lam, al.x, ex), fmaf(lam, al.y, ey));
             }
             if (lane == 0) f.s.st[0] = (uint8_t)VP_CH_FP64;
         } else {
-            if (lane < 16) write_channel_outputs_zero(f, K, M, lane);
+            if (lane < 16) write_channel_outputs_zero(f, K, M, Mp, lane);
             if (lane == 0) f.s.st[0] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
         }
         __syncwarp();
@@ -598,6 +617,8 @@ FactorArgs make_args(const vp_plan* p, const float2* H, int C, float2* U_out, fl
     a.K = p->K;
     a.M = p->M;
     a.n = p->n_paths;
+    a.Mp = p_rows(p);
+    a.lambda = p->lambda;
     a.kappa_thr = p->kappa_thr;
     a.d = p->d;
     a.U_out = U_out;
@@ -615,9 +636,11 @@ cudaError_t run_factor32(const FactorArgs& a, cudaStream_t s)
 {
     const int blocks = (a.C + kChPerBlock32 - 1) / kChPerBlock32;
     const int threads = kLanes * kChPerBlock32;
-    if (a.M <= 4) factor32_kernel<4><<<blocks, threads, 0, s>>>(a);
-    else if (a.M <= 8) factor32_kernel<8><<<blocks, threads, 0, s>>>(a);
-    else factor32_kernel<16><<<blocks, threads, 0, s>>>(a);
+    const int rows = a.lambda > 0.f ? a.M + a.K : a.M;   // rows of A = Hbar^H
+    if (rows <= 4) factor32_kernel<4><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 8) factor32_kernel<8><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 16) factor32_kernel<16><<<blocks, threads, 0, s>>>(a);
+    else factor32_kernel<32><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -651,6 +674,7 @@ cudaError_t launch_factor32_batch(const BatchProblem* probs, const int* ids, int
     a.C = count;
     a.K = K;
     a.M = M;
+    a.Mp = M;            // the batch table has lambda = 0
     a.kappa_thr = 0.f;   // per problem, read from the table
     a.probs = probs;
     a.ids = ids;

@@ -18,8 +18,10 @@ struct DeviceState {
     float2* utc = nullptr;     // [cap][K][K] U~ transposed (utc[m][l] = U~[l][m]), for the per-vector prologue
     float* w = nullptr;        // [cap][K]    w_l = U_ll^2 = 1 / R_ll^2
     uint8_t* ul = nullptr;     // [cap][K]    user at level l
-    float2* pt = nullptr;      // [cap][K][M] P^T in user order: pt[c][k][m] = P[m][k] (leading part)
-    float2* ptlo = nullptr;    // [cap][K][M] trailing part: P = pt + ptlo (zero where P is FP32-accurate)
+    float2* pt = nullptr;      // [cap][K][Mp] P^T in user order: pt[c][k][m] = P[m][k] (leading part)
+    float2* ptlo = nullptr;    // [cap][K][Mp] trailing part: P = pt + ptlo (zero where P is FP32-accurate)
+                               // Mp = M, or M + K with lambda > 0 (rows M.. map u to the
+                               // regularisation part of w = Qbar^H Rt u, Alg. 2)
     uint64_t* paths = nullptr; // [cap][n]    path codes, rank order
     uint64_t* maxq = nullptr;  // [cap][nchunk] per 32-path chunk, per level: max digit (4 bits/level)
     uint8_t* st = nullptr;     // [cap]       VP_CH_* bits
@@ -66,15 +68,15 @@ struct ChanState {
 
 __host__ __device__ inline int n_chunks(int n_paths) { return (n_paths + 31) / 32; }
 
-__host__ __device__ inline ChanState chan_state(const DeviceState& d, size_t c, int K, int M, int n)
+__host__ __device__ inline ChanState chan_state(const DeviceState& d, size_t c, int K, int Mp, int n)
 {
     ChanState s;
     s.utp = d.utp + c * K * K;
     s.utc = d.utc + c * K * K;
     s.w = d.w + c * K;
     s.ul = d.ul + c * K;
-    s.pt = d.pt + c * K * M;
-    s.ptlo = d.ptlo + c * K * M;
+    s.pt = d.pt + c * K * Mp;
+    s.ptlo = d.ptlo + c * K * Mp;
     s.paths = d.paths + c * n;
     s.maxq = d.maxq + c * n_chunks(n);
     s.st = d.st + c;
@@ -102,7 +104,9 @@ struct vp_plan {
     int K = 0, M = 0, qam = 0, n_paths = 0;
     float tau = 0.f;
     float kappa_thr = 1e4f;
+    float lambda = 0.f;   // Tikhonov parameter (Hbar = [H lambda*I])
     int cap = 0;   // channel capacity of `d`
+    int cap_mp = 0;  // rows of P that `d` was allocated for
     int C = 0;     // channels of the last vp_factorize
     vp::DeviceState d;
     // staging buffers of vp_run_slot_host
@@ -116,7 +120,11 @@ struct vp_plan {
 
 namespace vp {
 
-// Limits of one problem shape (those of vp_plan_create).
+// Rows of the precoding map w = Qbar^H Rt u kept per channel: the M antennas,
+// plus the K regularisation rows when lambda > 0.
+inline int p_rows(const vp_plan* p) { return p->M + (p->lambda > 0.f ? p->K : 0); }
+
+// Limits of one problem shape (those of vp_plan_create with lambda = 0).
 inline bool shape_ok(int K, int M, int qam, int n_paths, float tau)
 {
     if (K < 1 || K > VP_MAX_K || M < K || M > VP_MAX_M) return false;

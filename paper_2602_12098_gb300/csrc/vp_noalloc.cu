@@ -45,7 +45,7 @@ vp_status scratch_address(void** out)
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Lays the state of C channels out in the array; returns the bytes used.
-size_t carve(unsigned char* base, int C, int K, int M, int n, vp::DeviceState* d)
+size_t carve(unsigned char* base, int C, int K, int Mp, int n, vp::DeviceState* d)
 {
     const size_t nch = (size_t)vp::n_chunks(n);
     size_t off = 0;
@@ -58,8 +58,8 @@ size_t carve(unsigned char* base, int C, int K, int M, int n, vp::DeviceState* d
     d->utc = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * K));
     d->w = reinterpret_cast<float*>(take(sizeof(float) * C * K));
     d->ul = take((size_t)C * K);
-    d->pt = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * M));
-    d->ptlo = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * M));
+    d->pt = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * Mp));
+    d->ptlo = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * Mp));
     d->paths = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * n));
     d->maxq = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * nch));
     d->st = take((size_t)C);
@@ -78,14 +78,16 @@ vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const ui
                              int8_t* l, float* gamma, uint8_t* status, void* stream)
 {
     if (!plan || !H || !sym_idx || !x || !l || !gamma || C < 1 || S < 0) return VP_ERR_INVALID_ARG;
+    if (plan->K > plan->M && !(plan->lambda > 0.f)) return VP_ERR_INVALID_ARG;
+    const int mp = vp::p_rows(plan);
     vp::DeviceState probe;
-    if (carve(nullptr, C, plan->K, plan->M, plan->n_paths, &probe) > kNoAllocBytes) return VP_ERR_CAPACITY;
+    if (carve(nullptr, C, plan->K, mp, plan->n_paths, &probe) > kNoAllocBytes) return VP_ERR_CAPACITY;
     void* base = nullptr;
     vp_status st = scratch_address(&base);
     if (st != VP_OK) return st;
 
     vp_plan p = *plan;                    // parameters only; the state points into the array
-    carve(static_cast<unsigned char*>(base), C, p.K, p.M, p.n_paths, &p.d);
+    carve(static_cast<unsigned char*>(base), C, p.K, mp, p.n_paths, &p.d);
     p.cap = C;
     p.C = C;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

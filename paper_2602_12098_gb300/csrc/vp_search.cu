@@ -12,7 +12,9 @@
 // {-1,0,1}+j{-1,0,1} to r'_l (DEMAP), ties to the smaller (Re t, Im t).
 // The PED grows by w_l tau^2 |r'_l - t_l|^2.
 // The zero perturbation is candidate 0; the warp's (PED, index) minimum wins
-// (ties: lower index). x = P (s + tau l) / sqrt(gamma) with gamma = ||P u||^2,
+// (ties: lower index). w = P u with u = s + tau l, gamma = ||w||^2 and x = the
+// antenna rows of w / sqrt(gamma) (with lambda > 0, P has K more rows: the
+// regularisation part of Alg. 2's w, which counts in gamma but is not sent),
 // the product P u formed with exact products and compensated sums.
 #include "vp_internal.cuh"
 
@@ -29,6 +31,7 @@ struct SearchArgs {
     int8_t* l;
     float* gamma;
     int K, M, n, nch, m_qam;
+    int Mp;          // rows of P kept (M, or M + K with lambda > 0)
     float tau, inv_tau;
     DeviceState d;
     // batch mode (probs != null): block i works on problem ids[i] of the table;
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NW = blockDim.x >> 5;
     const int c = blockIdx.x;
-    int K, M, n, nch, m_qam;
+    int K, M, Mp, n, nch, m_qam;
     float tau, inv_tau;
     int v0, v1;
     ChanState cs;
@@ -257,14 +260,14 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     float* go;
     if (BATCH) {
         const BatchProblem& p = a.probs[a.ids[c]];
-        K = p.K; M = p.M; n = p.n; nch = n_chunks(p.n); m_qam = p.m_qam;
+        K = p.K; M = p.M; Mp = p.M; n = p.n; nch = n_chunks(p.n); m_qam = p.m_qam;
         tau = p.tau; inv_tau = 1.0f / p.tau;
         v0 = 0; v1 = p.S;
         cs = chan_state(p);
         sym = p.sym; xo = p.x; lo = p.l; go = p.gamma;
         if (threadIdx.x == 0 && p.status) p.status[0] = p.st[0];
     } else {
-        K = a.K; M = a.M; n = a.n; nch = a.nch; m_qam = a.m_qam;
+        K = a.K; M = a.M; Mp = a.Mp; n = a.n; nch = a.nch; m_qam = a.m_qam;
         tau = a.tau; inv_tau = a.inv_tau;
         if (a.off) {
             v0 = min(max(a.off[c], 0), a.n_vec);
@@ -273,10 +276,10 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
             v0 = c * a.S;
             v1 = v0 + a.S;
         }
-        cs = chan_state(a.d, (size_t)c, K, M, n);
+        cs = chan_state(a.d, (size_t)c, K, Mp, n);
         sym = a.sym; xo = a.x; lo = a.l; go = a.gamma;
     }
-    const int KM = BATCH ? a.KM : K * M, NP = BATCH ? a.NP : n;
+    const int KM = BATCH ? a.KM : K * Mp, NP = BATCH ? a.NP : n;
     const SearchSmem L = search_smem(KT, KM, NP, NW);
     float4* utp = reinterpret_cast<float4*>(smraw + L.utp);        // [KT][KT]
     float2* utc = reinterpret_cast<float2*>(smraw + L.utc);        // [KT][KT]
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         utp[i] = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         utc[i] = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
     }
-    for (int i = threadIdx.x; i < K * M; i += blockDim.x) {
+    for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
         pt[i] = cs.pt[i];
         ptl[i] = cs.ptlo[i];
     }
@@ -495,8 +498,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
         for (int lv = 0; lv < K; ++lv) {
             const float ur = __shfl_sync(kFull, u.x, lv), ui = __shfl_sync(kFull, u.y, lv);
-            if (lane < M) {
-                const int idx = ulv[lv] * M + lane;
+            if (lane < Mp) {
+                const int idx = ulv[lv] * Mp + lane;
                 const float2 ph = pt[idx], pl = ptl[idx];
                 dot2_acc(ph.x, ur, yr, yre);
                 dot2_acc(-ph.y, ui, yr, yre);
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
             }
         }
         const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
-        float g = (lane < M) ? cabs2(y) : 0.f;
+        float g = (lane < Mp) ? cabs2(y) : 0.f;     // ||w||^2 over all rows (Alg. 2's d)
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
         const float rs = __frsqrt_rn(g);
@@ -521,7 +524,7 @@ template <int KT>
 cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
 {
     const int NW = threads / 32;
-    const int KM = a.probs ? a.KM : a.K * a.M, NP = a.probs ? a.NP : a.n;
+    const int KM = a.probs ? a.KM : a.K * a.Mp, NP = a.probs ? a.NP : a.n;
     const size_t sh = (size_t)search_smem(KT, KM, NP, NW).total;
     if (a.probs) {
         static size_t attr = 0;
@@ -559,6 +562,7 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     a.gamma = gamma;
     a.K = p->K;
     a.M = p->M;
+    a.Mp = p_rows(p);
     a.n = p->n_paths;
     a.nch = n_chunks(p->n_paths);
     int m = 1;

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_plan_argument_validation():
-    bad = [(0, 4, 16, 16), (17, 17, 16, 16), (4, 3, 16, 16), (4, 4, 32, 16), (4, 4, 16, 0),
+    bad = [(0, 4, 16, 16), (17, 17, 16, 16), (4, 0, 16, 16), (4, 4, 32, 16), (4, 4, 16, 0),
            (2, 2, 16, 82), (4, 4, 16, 2000), (4, 17, 16, 16)]
     for K, M, q, n in bad:
         with pytest.raises(vp.VPError) as e:
@@ -103,3 +103,20 @@ def test_batch_validation_and_grouping():
         vp.vp_batch_destroy(b)
     with pytest.raises(vp.VPError):
         vp.vp_batch_create(good, fp64_threshold=float("nan"))
+
+
+def test_overloaded_plan_needs_lambda():
+    """K > M is a valid plan, but factorising it needs lambda > 0 (checked on
+    the host before any device work)."""
+    h = vp.vp_plan_create(8, 4, 4, 64)
+    try:
+        with pytest.raises(vp.VPError) as e:
+            vp.vp_factorize(h, 256, 2, stream=0)
+        assert e.value.code == 1
+        for bad in (-0.5, float("nan"), float("inf")):
+            with pytest.raises(vp.VPError):
+                vp.vp_plan_set_lambda(h, bad)
+        vp.vp_plan_set_lambda(h, 0.5)
+        vp.vp_plan_set_lambda(h, 0.0)
+    finally:
+        vp.vp_plan_destroy(h)

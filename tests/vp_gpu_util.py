@@ -18,7 +18,7 @@ GAMMA_RTOL = 1e-5
 X_RTOL = 1e-5
 
 
-def run_gpu(H, sym, vec_off, qam, n, tau=0.0, fp64_threshold=None, want_factor=True, uniform_S=None):
+def run_gpu(H, sym, vec_off, qam, n, tau=0.0, fp64_threshold=None, want_factor=True, uniform_S=None, lam=0.0):
     """Whole path on cuda:0 through the C-ABI. Returns numpy outputs."""
     dev = torch.device("cuda:0")
     C, K, M = H.shape
@@ -34,7 +34,7 @@ def run_gpu(H, sym, vec_off, qam, n, tau=0.0, fp64_threshold=None, want_factor=T
     ul = torch.zeros((C, K), dtype=torch.uint8, device=dev) if want_factor else None
     st = torch.zeros((C,), dtype=torch.uint8, device=dev)
     codes = torch.zeros((C, n), dtype=torch.int64, device=dev)
-    with vp.Plan(K, M, qam, n, tau, fp64_threshold) as plan:
+    with vp.Plan(K, M, qam, n, tau, fp64_threshold, lam=lam) as plan:
         vp.vp_factorize(plan.handle, Hd, C, U, P, ul, st)
         if uniform_S is not None:
             vp.vp_precode(plan.handle, symd, uniform_S, None, V, x, l, g)
@@ -49,9 +49,9 @@ def run_gpu(H, sym, vec_off, qam, n, tau=0.0, fp64_threshold=None, want_factor=T
     return out
 
 
-def oracle_x_at(orc, H, qam, tau, l_user, sym_user):
+def oracle_x_at(orc, H, qam, tau, l_user, sym_user, lam=0.0):
     """Oracle x and gamma for a GIVEN perturbation (user order), from its factor."""
-    f = orc.factor_channel(H.astype(np.complex128), 1)
+    f = orc.factor_channel(H.astype(np.complex128), 1, lam)
     ul = f["user_of_level"]
     s = orc.qam_points(qam, sym_user)
     u = s + tau * (l_user[:, 0] + 1j * l_user[:, 1])
@@ -61,7 +61,7 @@ def oracle_x_at(orc, H, qam, tau, l_user, sym_user):
     return w / np.sqrt(gam), gam
 
 
-def compare(orc, H, sym, vec_off, qam, gpu, ref, tau=None):
+def compare(orc, H, sym, vec_off, qam, gpu, ref, tau=None, lam=0.0):
     """Element-wise comparison; returns a stats dict (asserts nothing)."""
     tau = orc.default_tau(qam) if tau is None else tau
     V = sym.shape[0]
@@ -76,7 +76,7 @@ def compare(orc, H, sym, vec_off, qam, gpu, ref, tau=None):
         st["x_err_max"] = float(np.max(np.linalg.norm(gpu["x"][m] - ref["x"][m], axis=1)))
     for v in np.nonzero(~l_eq & good)[0]:
         c = ch_of[v]
-        xg, gg = oracle_x_at(orc, H[c], qam, tau, gpu["l"][v].astype(np.int64), sym[v])
+        xg, gg = oracle_x_at(orc, H[c], qam, tau, gpu["l"][v].astype(np.int64), sym[v], lam)
         st["tie_gamma_rel_max"] = max(st["tie_gamma_rel_max"], (gg - ref["gamma"][v]) / ref["gamma"][v])
         st["tie_x_err_max"] = max(st["tie_x_err_max"], float(np.linalg.norm(gpu["x"][v] - xg)))
         st["gamma_rel_max"] = max(st["gamma_rel_max"], abs(gpu["gamma"][v] - gg) / gg)
