@@ -26,6 +26,10 @@ void free_state(vp::DeviceState& d)
     cudaFree(d.ptlo);
     cudaFree(d.paths);
     cudaFree(d.maxq);
+    cudaFree(d.ecode);
+    cudaFree(d.emeta);
+    cudaFree(d.pcode);
+    cudaFree(d.phdr);
     cudaFree(d.st);
     cudaFree(d.nflag);
     cudaFree(d.flags);
@@ -50,7 +54,9 @@ vp_status ensure_capacity(vp_plan* p, int C)
     vp::DeviceState d;
     bool ok = dalloc(&d.utp, (size_t)C * K * K) && dalloc(&d.utc, (size_t)C * K * K) &&
               dalloc(&d.w, (size_t)C * K) && dalloc(&d.ul, (size_t)C * K) && dalloc(&d.pt, (size_t)C * K * M) && dalloc(&d.ptlo, (size_t)C * K * M) &&
-              dalloc(&d.paths, (size_t)C * n) && dalloc(&d.maxq, (size_t)C * nch) && dalloc(&d.st, (size_t)C) &&
+              dalloc(&d.paths, (size_t)C * n) && dalloc(&d.maxq, (size_t)C * nch) && dalloc(&d.ecode, (size_t)C * n) &&
+              dalloc(&d.emeta, (size_t)C * n) && dalloc(&d.pcode, (size_t)C * vp::kMaxPrefix) &&
+              dalloc(&d.phdr, (size_t)C) && dalloc(&d.st, (size_t)C) &&
               dalloc(&d.nflag, 1) && dalloc(&d.flags, (size_t)C);
     if (!ok) {
         free_state(d);

@@ -40,11 +40,13 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Per-problem state, in the order utp, utc, pt, ptlo, paths, maxq, w, ul, st.
+// Per-problem state, in the order phdr, utp, utc, pt, ptlo, paths, maxq,
+// ecode, pcode, emeta, w, ul, st (16-byte parts first).
 size_t state_bytes(int K, int M, int n)
 {
-    size_t b = 16 * (size_t)K * K;
+    size_t b = 16 + 16 * (size_t)K * K;
     b += 8 * (size_t)K * K + 16 * (size_t)K * M + 8 * (size_t)n + 8 * (size_t)vp::n_chunks(n);
+    b += 8 * (size_t)n + 8 * (size_t)vp::kMaxPrefix + 4 * (size_t)n;
     b += 4 * (size_t)K + (size_t)K + 1;
     return align_up(b, 16);
 }
@@ -155,6 +157,8 @@ void fill_table(vp_batch* b)
         vp::BatchProblem& p = b->table[i];
         const int K = d.K, M = d.M, n = d.n_paths;
         unsigned char* q = base + b->state_off[i];
+        p.phdr = reinterpret_cast<int4*>(q);
+        q += 16;
         p.utp = reinterpret_cast<float4*>(q);
         q += 16 * (size_t)K * K;
         p.utc = reinterpret_cast<float2*>(q);
@@ -167,6 +171,12 @@ void fill_table(vp_batch* b)
         q += 8 * (size_t)n;
         p.maxq = reinterpret_cast<uint64_t*>(q);
         q += 8 * (size_t)vp::n_chunks(n);
+        p.ecode = reinterpret_cast<uint64_t*>(q);
+        q += 8 * (size_t)n;
+        p.pcode = reinterpret_cast<uint64_t*>(q);
+        q += 8 * (size_t)vp::kMaxPrefix;
+        p.emeta = reinterpret_cast<uint32_t*>(q);
+        q += 4 * (size_t)n;
         p.w = reinterpret_cast<float*>(q);
         q += 4 * (size_t)K;
         p.ul = q;

@@ -11,6 +11,10 @@ namespace vp {
 constexpr int kMaxK = VP_MAX_K;
 constexpr int kMaxM = VP_MAX_M;
 constexpr int kMaxPaths = VP_MAX_PATHS;
+// The search evaluates the top T <= kSplitMax levels once per distinct path
+// prefix (at most kMaxPrefix of them, one lane each).
+constexpr int kMaxPrefix = 32;
+constexpr int kSplitMax = 3;
 
 // Resident per-channel state of a plan (device pointers, capacity `cap` channels).
 struct DeviceState {
@@ -23,7 +27,11 @@ struct DeviceState {
                                // Mp = M, or M + K with lambda > 0 (rows M.. map u to the
                                // regularisation part of w = Qbar^H Rt u, Alg. 2)
     uint64_t* paths = nullptr; // [cap][n]    path codes, rank order
-    uint64_t* maxq = nullptr;  // [cap][nchunk] per 32-path chunk, per level: max digit (4 bits/level)
+    uint64_t* maxq = nullptr;  // [cap][nchunk] per 32-path chunk of the evaluation order, per level: max digit
+    uint64_t* ecode = nullptr; // [cap][n]    path codes in evaluation order
+    uint32_t* emeta = nullptr; // [cap][n]    MoP rank | shared-prefix index << 16, evaluation order
+    uint64_t* pcode = nullptr; // [cap][kMaxPrefix] a code of each shared prefix
+    int4* phdr = nullptr;      // [cap]       shared levels T, prefix count, per-level max digit of the prefixes
     uint8_t* st = nullptr;     // [cap]       VP_CH_* bits
     int* nflag = nullptr;      // [1]         number of channels sent to the FP64 path
     int* flags = nullptr;      // [cap]       their indices
@@ -47,6 +55,10 @@ struct BatchProblem {
     float2* ptlo;
     uint64_t* paths;
     uint64_t* maxq;
+    uint64_t* ecode;
+    uint32_t* emeta;
+    uint64_t* pcode;
+    int4* phdr;
     uint8_t* st;
     int K, M, n, m_qam, S;
     float tau, kappa_thr;
@@ -63,10 +75,27 @@ struct ChanState {
     float2* ptlo;
     uint64_t* paths;
     uint64_t* maxq;
+    uint64_t* ecode;
+    uint32_t* emeta;
+    uint64_t* pcode;
+    int4* phdr;
     uint8_t* st;
 };
 
 __host__ __device__ inline int n_chunks(int n_paths) { return (n_paths + 31) / 32; }
+
+// K tile of the search kernel (levels unrolled); the shared top levels are
+// used when K fills its tile (K = 8, 12, 16).
+__host__ __device__ inline int search_tile(int K) { return K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16; }
+
+// The K 4-bit digits of a path code in reverse level order (an involution).
+__device__ __forceinline__ uint64_t nibble_reverse(uint64_t c, int K)
+{
+    c = __brevll(c);                                                                 // bits reversed
+    c = ((c >> 1) & 0x5555555555555555ull) | ((c & 0x5555555555555555ull) << 1);
+    c = ((c >> 2) & 0x3333333333333333ull) | ((c & 0x3333333333333333ull) << 2);    // nibbles restored
+    return K == 16 ? c : c >> (64 - 4 * K);
+}
 
 __host__ __device__ inline ChanState chan_state(const DeviceState& d, size_t c, int K, int Mp, int n)
 {
@@ -79,6 +108,10 @@ __host__ __device__ inline ChanState chan_state(const DeviceState& d, size_t c, 
     s.ptlo = d.ptlo + c * K * Mp;
     s.paths = d.paths + c * n;
     s.maxq = d.maxq + c * n_chunks(n);
+    s.ecode = d.ecode + c * n;
+    s.emeta = d.emeta + c * n;
+    s.pcode = d.pcode + c * kMaxPrefix;
+    s.phdr = d.phdr + c;
     s.st = d.st + c;
     return s;
 }
@@ -94,6 +127,10 @@ __host__ __device__ inline ChanState chan_state(const BatchProblem& p)
     s.ptlo = p.ptlo;
     s.paths = p.paths;
     s.maxq = p.maxq;
+    s.ecode = p.ecode;
+    s.emeta = p.emeta;
+    s.pcode = p.pcode;
+    s.phdr = p.phdr;
     s.st = p.st;
     return s;
 }

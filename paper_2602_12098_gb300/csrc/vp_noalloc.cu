@@ -62,6 +62,10 @@ size_t carve(unsigned char* base, int C, int K, int Mp, int n, vp::DeviceState* 
     d->ptlo = reinterpret_cast<float2*>(take(sizeof(float2) * C * K * Mp));
     d->paths = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * n));
     d->maxq = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * nch));
+    d->ecode = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * n));
+    d->emeta = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * C * n));
+    d->pcode = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * C * vp::kMaxPrefix));
+    d->phdr = reinterpret_cast<int4*>(take(sizeof(int4) * C));
     d->st = take((size_t)C);
     d->nflag = reinterpret_cast<int*>(take(sizeof(int)));
     d->flags = reinterpret_cast<int*>(take(sizeof(int) * C));

@@ -28,6 +28,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct PathArgs {
     int C, K, n, nch;
     int ns;                     // skewed list length of the launch's largest n
+    int gstride;                // shared memory of one channel group, in 8-byte words
     DeviceState d;
     const BatchProblem* probs;  // batch mode: channel i of the launch is problem ids[i]
     const int* ids;
@@ -86,6 +87,145 @@ __device__ void merge_shift(const uint64_t* Am, const uint64_t* Ac, int na,
     }
 }
 
+// Evaluation order of a channel's paths for the search, computed once per
+// channel (every vector of the channel uses it):
+//  1. shared top levels: presence bitmaps of the top-1/2/3-level prefixes
+//     give the largest T <= kSplitMax whose distinct prefixes fit one pass of
+//     kMaxPrefix lanes (when K fills its search tile and there are 2+
+//     chunks); a path's prefix index is its prefix's rank in the bitmap;
+//  2. evaluation order: the paths sorted by their digits from level 1 up (the
+//     light levels, where the candidates differ most), so that a 32-path
+//     chunk shares small digits and needs the cheap DEMAP branches (results
+//     do not depend on the order: ties are broken by MoP rank);
+//  3. per chunk and level the largest digit, and over the prefixes.
+// The group's list buffers are reused (the paths were already written to
+// `out`, which is read back after the barrier).
+__host__ __device__ inline int pow2_ceil(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+__host__ __device__ inline size_t eval_order_bytes(int n) { return 12 * (size_t)pow2_ceil(n) + 8 + 1664; }
+
+__device__ void eval_order(const ChanState& cs, const uint64_t* out, uint64_t* base, int n, int K, int nch, int t,
+                           int tpc)
+{
+    constexpr int kBits = 16 * 16 * 16;                          // top three digits
+    auto gsync = [&]() {
+        if (tpc == 32) __syncwarp(kFull);
+        else __syncthreads();
+    };
+    const int lane = t & 31, wig = t >> 5, nwarp = tpc >> 5;
+    const int np2 = pow2_ceil(n);
+    uint64_t* key = base;                                                  // [np2] sort keys
+    uint32_t* val = reinterpret_cast<uint32_t*>(base + np2);               // [np2] rank | prefix << 16
+    uint64_t* pcs = base + np2 + (np2 + 1) / 2;                            // [kMaxPrefix] prefix codes
+    uint32_t* bm3 = reinterpret_cast<uint32_t*>(pcs + kMaxPrefix);         // [128] prefixes of 3 levels
+    int* wpre = reinterpret_cast<int*>(bm3 + kBits / 32);                  // [128] set bits before a word
+    uint32_t* bm2 = reinterpret_cast<uint32_t*>(wpre + kBits / 32);        // [8]
+    uint32_t* bm1 = bm2 + 8;                                               // [1]
+    gsync();
+    for (int i = t; i < kBits / 32; i += tpc) bm3[i] = 0u;
+    for (int i = t; i < 8; i += tpc) bm2[i] = 0u;
+    if (t == 0) bm1[0] = 0u;
+    gsync();
+    const bool split = K == search_tile(K) && K >= 8 && nch >= 2;
+    if (split) {
+        for (int i = t; i < n; i += tpc) {
+            const unsigned p3 = (unsigned)(out[i] >> (4 * (K - 3))) & 0xfffu;
+            atomicOr(&bm3[p3 >> 5], 1u << (p3 & 31));
+            atomicOr(&bm2[(p3 >> 4) >> 5], 1u << ((p3 >> 4) & 31));
+            atomicOr(&bm1[0], 1u << (p3 >> 8));
+        }
+    }
+    gsync();
+    int T = 0;
+    if (split) {
+        int n3 = 0, n2 = 0;
+        for (int w = 0; w < kBits / 32; ++w) n3 += __popc(bm3[w]);
+        for (int w = 0; w < 8; ++w) n2 += __popc(bm2[w]);
+        const int n1 = __popc(bm1[0]);
+        T = n3 <= kMaxPrefix ? 3 : (n2 <= kMaxPrefix ? 2 : (n1 <= kMaxPrefix ? 1 : 0));
+    }
+    if (T == 3) {
+        for (int w = t; w < kBits / 32; w += tpc) {
+            int r = 0;
+            for (int w2 = 0; w2 < w; ++w2) r += __popc(bm3[w2]);
+            wpre[w] = r;
+        }
+    } else if (T == 2 && t < 8) {
+        int r = 0;
+        for (int w2 = 0; w2 < t; ++w2) r += __popc(bm2[w2]);
+        wpre[t] = r;
+    }
+    gsync();
+    const int npf = T == 3 ? wpre[kBits / 32 - 1] + __popc(bm3[kBits / 32 - 1])
+                  : T == 2 ? wpre[7] + __popc(bm2[7])
+                  : T == 1 ? __popc(bm1[0]) : 1;
+    for (int i = t; i < np2; i += tpc) {
+        if (i >= n) {
+            key[i] = ~0ull;
+            val[i] = 0u;
+            continue;
+        }
+        const uint64_t c = out[i];
+        int p = 0;
+        if (T > 0) {
+            const unsigned pv = (unsigned)(c >> (4 * (K - T))) & ((1u << (4 * T)) - 1u);
+            if (T == 3) p = wpre[pv >> 5] + __popc(bm3[pv >> 5] & ((1u << (pv & 31)) - 1u));
+            else if (T == 2) p = wpre[pv >> 5] + __popc(bm2[pv >> 5] & ((1u << (pv & 31)) - 1u));
+            else p = __popc(bm1[0] & ((1u << pv) - 1u));
+            pcs[p] = c;                                          // any code with this prefix
+        }
+        key[i] = nibble_reverse(c, K);
+        val[i] = (uint32_t)i | ((uint32_t)p << 16);
+    }
+    if (T == 0 && t == 0) pcs[0] = 0ull;
+    gsync();
+    for (int k = 2; k <= np2; k <<= 1) {                         // ascending bitonic sort, keys distinct
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < (np2 >> 1); i += tpc) {
+                const int ix = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                const int iy = ix + j;
+                const bool up = (ix & k) == 0;
+                const uint64_t c0 = key[ix], c1 = key[iy];
+                if ((c0 > c1) == up && c0 != c1) {
+                    key[ix] = c1;
+                    key[iy] = c0;
+                    const uint32_t v = val[ix];
+                    val[ix] = val[iy];
+                    val[iy] = v;
+                }
+            }
+            gsync();
+        }
+    }
+    for (int i = t; i < n; i += tpc) {
+        const uint64_t c = nibble_reverse(key[i], K);
+        key[i] = c;
+        cs.ecode[i] = c;
+        cs.emeta[i] = val[i];
+    }
+    for (int i = t; i < kMaxPrefix; i += tpc) cs.pcode[i] = i < npf ? pcs[i] : 0ull;
+    gsync();
+    for (int ch = wig; ch < nch; ch += nwarp) {
+        const int i = ch * 32 + lane;
+        const uint64_t code = i < n ? key[i] : 0ull;
+        uint64_t mq = 0;
+        for (int l = 0; l < K; ++l)
+            mq |= (uint64_t)__reduce_max_sync(kFull, (unsigned)((code >> (4 * l)) & 15u)) << (4 * l);
+        if (lane == 0) cs.maxq[ch] = mq;
+    }
+    if (wig == 0) {
+        const uint64_t code = lane < npf ? pcs[lane] : 0ull;
+        uint64_t mq = 0;
+        for (int l = K - T; l < K; ++l)
+            mq |= (uint64_t)__reduce_max_sync(kFull, (unsigned)((code >> (4 * l)) & 15u)) << (4 * l);
+        if (lane == 0) cs.phdr[0] = make_int4(T, npf, (int)(uint32_t)mq, (int)(uint32_t)(mq >> 32));
+    }
+}
+
 // A channel is worked on by `tpc` threads: one warp (a block then holds `cpb`
 // channels) or a whole block of 2-4 warps (cpb = 1), which shortens the
 // dependent merge chains of a channel. Shared memory: 48 n bytes per channel.
@@ -111,7 +251,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
         cs = chan_state(a.d, (size_t)ci, K, 0, n);
     }
     const int ns = sk(n);                                        // skewed length of one list
-    uint64_t* base = shm + (size_t)grp * 6 * a.ns;
+    uint64_t* base = shm + (size_t)grp * a.gstride;
     // buffer b (0..2): metrics at base + 2 b ns, codes at base + (2 b + 1) ns
     // (pointer arithmetic: an indexed pointer array would live in local memory)
 #define BM(b) (base + 2 * (b) * ns)
@@ -124,6 +264,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
     if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
         for (int i = t; i < n; i += tpc) out[i] = 0;
         for (int i = t; i < nch; i += tpc) mqo[i] = 0;
+        if (t == 0) cs.phdr[0] = make_int4(0, 1, 0, 0);
         return;
     }
     if (wig == 0) {
@@ -176,24 +317,17 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
 #undef BM
 #undef BC
     for (int i = t; i < n; i += tpc) out[i] = (i < s) ? Sc[sk(i)] : 0;
-    for (int ch = wig; ch < nch; ch += tpc >> 5) {
-        const int i = ch * 32 + lane;
-        const uint64_t code = (i < s) ? Sc[sk(i)] : 0;
-        uint64_t mq = 0;
-        for (int l = 0; l < K; ++l) {
-            const unsigned dgt = (unsigned)((code >> (4 * l)) & 15u);
-            mq |= (uint64_t)__reduce_max_sync(kFull, dgt) << (4 * l);
-        }
-        if (lane == 0) mqo[ch] = mq;
-    }
+    eval_order(cs, out, base, n, K, nch, t, tpc);
 }
 
 cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
 {
     const int ns = n_max + (n_max >> 3);
     a.ns = ns;
-    const size_t per = (size_t)6 * ns * sizeof(uint64_t);
+    size_t per = (size_t)6 * ns * sizeof(uint64_t);
+    if (per < eval_order_bytes(n_max)) per = (eval_order_bytes(n_max) + 15) & ~size_t(15);
     // long lists: a block of warps per channel; short ones: a warp per channel
+    a.gstride = (int)(per / sizeof(uint64_t));
     const int tpc = n_max >= 128 ? 64 : 32;
     int cpb = 1;
     if (tpc == 32) {

@@ -157,13 +157,6 @@ __device__ __forceinline__ void level_step(int lv, const float4* utp, const floa
     }
 }
 
-__host__ __device__ inline int pow2_at_least(int x)
-{
-    int p = 32;
-    while (p < x) p <<= 1;
-    return p;
-}
-
 __host__ __device__ inline int take16(int& o, int bytes)
 {
     const int r = o;
@@ -171,75 +164,38 @@ __host__ __device__ inline int take16(int& o, int bytes)
     return r;
 }
 
-// Ascending bitonic sort of key[0..np2) (np2 a power of two, keys distinct
-// except the padding) carrying val; every thread of the block calls it.
-__device__ void block_sort(uint64_t* key, uint32_t* val, int np2)
-{
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < (np2 >> 1); i += blockDim.x) {
-                const int ix = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-                const int iy = ix + j;
-                const bool up = (ix & k) == 0;
-                const uint64_t c0 = key[ix], c1 = key[iy];
-                if ((c0 > c1) == up && c0 != c1) {
-                    key[ix] = c1;
-                    key[iy] = c0;
-                    const uint32_t t = val[ix];
-                    val[ix] = val[iy];
-                    val[iy] = t;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// The K 4-bit digits of a path code in reverse level order (an involution).
-__device__ __forceinline__ uint64_t nibble_reverse(uint64_t c, int K)
-{
-    c = __brevll(c);                                                        // bits reversed
-    c = ((c >> 1) & 0x5555555555555555ull) | ((c & 0x5555555555555555ull) << 1);
-    c = ((c >> 2) & 0x3333333333333333ull) | ((c & 0x3333333333333333ull) << 2);   // nibbles restored
-    return K == 16 ? c : c >> (64 - 4 * K);
-}
-
-constexpr int kMaxPrefix = 32;   // distinct top-level prefixes evaluated once per vector (one lane each)
-constexpr int kSplitMax = 3;     // at most this many top levels are shared
 
 // Shared-memory layout of one search block (byte offsets, 16-byte aligned).
 struct SearchSmem {
-    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, scrl, scrp, wv, ulv, meta, misc, total;
+    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, scrl, scrp, wv, ulv, meta, total;
 };
 
 __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW)
 {
     SearchSmem s;
     int o = 0;
-    const int np2 = pow2_at_least(NP);
     s.utp = take16(o, 16 * KT * KT);
     s.utc = take16(o, 8 * KT * KT);
     s.pt = take16(o, 8 * KM);
     s.ptl = take16(o, 8 * KM);
     s.bvec = take16(o, 8 * NW * KT);
     s.scr = take16(o, 8 * NW * KT * kMaxPrefix);
-    s.tc = take16(o, 8 * np2);
+    s.tc = take16(o, 8 * NP);
     s.tmq = take16(o, 8 * n_chunks(NP));
     s.pcode = take16(o, 8 * kMaxPrefix);
     s.scrl = take16(o, 8 * NW * kMaxPrefix);
     s.scrp = take16(o, 4 * NW * kMaxPrefix);
     s.wv = take16(o, 4 * KT);
     s.ulv = take16(o, 4 * KT);
-    s.meta = take16(o, 4 * np2);
-    s.misc = take16(o, 4 * (4 + 32) + 8);
+    s.meta = take16(o, 4 * NP);
     s.total = o;
     return s;
 }
 
-// Per channel (block): the candidate paths are re-sorted into trie order
-// (code ascending = lexicographic from level K down) with their MoP rank kept
-// for tie-breaking. The top T <= 3 levels of the distinct prefixes
-// (<= 32 of them) are evaluated once per vector, one lane per prefix, and
+// Per channel (block): path selection left the paths in evaluation order
+// with their MoP rank (for tie-breaking) and shared-prefix index, the
+// distinct prefixes of the top T <= 3 levels (<= 32 of them) and the digit
+// maxima. Per vector the prefixes are evaluated once, one lane each, and
 // their residuals, PED and chosen points stored in shared memory; every path
 // then continues from its prefix's state through the remaining levels. The
 // arithmetic per path is the same as a full descent, so results are
@@ -287,16 +243,14 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     float2* ptl = reinterpret_cast<float2*>(smraw + L.ptl);        // [K][M] trailing part
     float2* bvec = reinterpret_cast<float2*>(smraw + L.bvec);      // [NW][KT]
     float2* scr_all = reinterpret_cast<float2*>(smraw + L.scr);    // [NW][KT][32] prefix residuals
-    uint64_t* tc = reinterpret_cast<uint64_t*>(smraw + L.tc);      // [np2] codes, trie order
-    uint64_t* tmq = reinterpret_cast<uint64_t*>(smraw + L.tmq);    // [nch] chunk digit maxima, trie order
+    uint64_t* tc = reinterpret_cast<uint64_t*>(smraw + L.tc);      // [n] codes, evaluation order
+    uint64_t* tmq = reinterpret_cast<uint64_t*>(smraw + L.tmq);    // [nch] chunk digit maxima, evaluation order
     uint64_t* pcode = reinterpret_cast<uint64_t*>(smraw + L.pcode);// [32] a code of each prefix
     uint2* scrl_all = reinterpret_cast<uint2*>(smraw + L.scrl);    // [NW][32] prefix chosen points
     float* scrp_all = reinterpret_cast<float*>(smraw + L.scrp);    // [NW][32] prefix PED
     float* wv = reinterpret_cast<float*>(smraw + L.wv);            // [KT]
     int* ulv = reinterpret_cast<int*>(smraw + L.ulv);              // [KT]
-    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + L.meta);  // [np2] MoP rank | prefix << 16
-    int* misc = reinterpret_cast<int*>(smraw + L.misc);            // counts [4], per-chunk starts [32]
-    uint64_t* amq_s = reinterpret_cast<uint64_t*>(misc + 36);
+    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + L.meta);  // [n] MoP rank | prefix << 16
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
@@ -311,7 +265,6 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         return;
     }
 
-    const int np2 = pow2_at_least(n);
     for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
         const int r = i / KT, q = i % KT;
         const bool in = r < K && q < K;
@@ -322,80 +275,24 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         pt[i] = cs.pt[i];
         ptl[i] = cs.ptlo[i];
     }
-    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-        tc[i] = i < n ? cs.paths[i] : ~0ull;
-        meta[i] = (uint32_t)i;
+    // evaluation order, shared prefixes and chunk digit maxima (from path selection)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tc[i] = cs.ecode[i];
+        meta[i] = cs.emeta[i];
     }
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) tmq[i] = cs.maxq[i];
+    for (int i = threadIdx.x; i < kMaxPrefix; i += blockDim.x) pcode[i] = cs.pcode[i];
     for (int i = threadIdx.x; i < KT; i += blockDim.x) {
         wv[i] = i < K ? cs.w[i] * tau * tau : 0.f;   // w_l tau^2
         ulv[i] = i < K ? (int)cs.ul[i] : 0;
     }
-    if (threadIdx.x < 4) misc[threadIdx.x] = 0;
+    const int4 hdr = cs.phdr[0];
+    const int T = (K == KT) ? hdr.x : 0;   // shared top levels (0 when K does not fill the tile)
+    const int NPF = T > 0 ? hdr.y : 1;
+    const uint64_t amq = (uint64_t)(uint32_t)hdr.z | ((uint64_t)(uint32_t)hdr.w << 32);
+    if (T == 0 && threadIdx.x == 0) pcode[0] = 0ull;
     __syncthreads();
 
-    // trie order (code ascending: lexicographic from level K down) to find the prefixes
-    block_sort(tc, meta, np2);
-
-    // shared top levels: the largest T <= 3 whose distinct prefixes fit the lanes of one pass
-    int T = 0;
-    if (K == KT && KT >= 8 && nch >= 2) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-#pragma unroll
-            for (int t = 1; t <= kSplitMax; ++t) {
-                const int sh = 4 * (K - t);
-                if (i == 0 || (tc[i] >> sh) != (tc[i - 1] >> sh)) atomicAdd(&misc[t], 1);
-            }
-        }
-        __syncthreads();
-        T = kSplitMax;
-        while (T > 0 && misc[T] > kMaxPrefix) --T;
-    }
-    const int psh = 4 * (K - T);   // prefix = code >> psh (T = 0: one empty prefix)
-    for (int ch = warp; ch < nch; ch += NW) {
-        const int i = ch * 32 + lane;
-        const bool st = i < n && (i == 0 || (T > 0 && (tc[i] >> psh) != (tc[i - 1] >> psh)));
-        const unsigned bal = __ballot_sync(kFull, st);
-        if (lane == 0) misc[4 + ch] = __popc(bal);
-    }
-    __syncthreads();
-    for (int ch = warp; ch < nch; ch += NW) {
-        int base = 0;
-        for (int c2 = 0; c2 < ch; ++c2) base += misc[4 + c2];
-        const int i = ch * 32 + lane;
-        const bool st = i < n && (i == 0 || (T > 0 && (tc[i] >> psh) != (tc[i - 1] >> psh)));
-        const unsigned bal = __ballot_sync(kFull, st);
-        const int incl = base + __popc(bal & (0xffffffffu >> (31 - lane)));
-        if (i < n) meta[i] |= (uint32_t)(incl - 1) << 16;
-        if (st) pcode[incl - 1] = tc[i];
-    }
-    __syncthreads();
-    // evaluation order: level 1 most significant (the light levels, where the
-    // candidates' digits differ most), so a 32-path chunk shares small digits
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tc[i] = nibble_reverse(tc[i], K);
-    __syncthreads();
-    block_sort(tc, meta, np2);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tc[i] = nibble_reverse(tc[i], K);
-    __syncthreads();
-    for (int ch = warp; ch < nch; ch += NW) {
-        const int i = ch * 32 + lane;
-        const uint64_t code = i < n ? tc[i] : 0ull;
-        uint64_t mq = 0;
-        for (int l = 0; l < K; ++l)
-            mq |= (uint64_t)__reduce_max_sync(kFull, (unsigned)((code >> (4 * l)) & 15u)) << (4 * l);
-        if (lane == 0) tmq[ch] = mq;
-    }
-    __syncthreads();
-    const int NPF = T > 0 ? misc[T] : 1;
-    if (warp == 0) {
-        const uint64_t code = lane < NPF ? pcode[lane] : 0ull;
-        uint64_t mq = 0;
-        for (int l = K - T; l < K; ++l)
-            mq |= (uint64_t)__reduce_max_sync(kFull, (unsigned)((code >> (4 * l)) & 15u)) << (4 * l);
-        if (lane == 0) *amq_s = mq;
-    }
-    __syncthreads();
-
-    const uint64_t amq = *amq_s;
     float2* bw = bvec + warp * KT;
     float2* scr = scr_all + warp * KT * kMaxPrefix;
     float* scrp = scrp_all + warp * kMaxPrefix;
