@@ -142,22 +142,36 @@ __device__ void eval_order(const ChanState& cs, const uint64_t* out, uint64_t* b
     gsync();
     int T = 0;
     if (split) {
-        int n3 = 0, n2 = 0;
-        for (int w = 0; w < kBits / 32; ++w) n3 += __popc(bm3[w]);
-        for (int w = 0; w < 8; ++w) n2 += __popc(bm2[w]);
+        // every warp counts the set bits (lane l: words 4l..4l+3 of the 3-level map)
+        const int c4 = __popc(bm3[4 * lane]) + __popc(bm3[4 * lane + 1]) + __popc(bm3[4 * lane + 2]) +
+                       __popc(bm3[4 * lane + 3]);
+        int incl = c4;                                           // inclusive scan over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int n3 = __shfl_sync(kFull, incl, 31);
+        int c2 = lane < 8 ? __popc(bm2[lane]) : 0, i2 = c2;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, i2, o);
+            if (lane >= o) i2 += v;
+        }
+        const int n2 = __shfl_sync(kFull, i2, 7);
         const int n1 = __popc(bm1[0]);
         T = n3 <= kMaxPrefix ? 3 : (n2 <= kMaxPrefix ? 2 : (n1 <= kMaxPrefix ? 1 : 0));
-    }
-    if (T == 3) {
-        for (int w = t; w < kBits / 32; w += tpc) {
-            int r = 0;
-            for (int w2 = 0; w2 < w; ++w2) r += __popc(bm3[w2]);
-            wpre[w] = r;
+        if (wig == 0) {                                          // words' exclusive prefix counts
+            if (T == 3) {
+                int r = incl - c4;
+                for (int q = 0; q < 4; ++q) {
+                    wpre[4 * lane + q] = r;
+                    r += __popc(bm3[4 * lane + q]);
+                }
+            } else if (T == 2 && lane < 8) {
+                wpre[lane] = i2 - c2;
+            }
         }
-    } else if (T == 2 && t < 8) {
-        int r = 0;
-        for (int w2 = 0; w2 < t; ++w2) r += __popc(bm2[w2]);
-        wpre[t] = r;
     }
     gsync();
     const int npf = T == 3 ? wpre[kBits / 32 - 1] + __popc(bm3[kBits / 32 - 1])
@@ -183,7 +197,7 @@ __device__ void eval_order(const ChanState& cs, const uint64_t* out, uint64_t* b
     }
     if (T == 0 && t == 0) pcs[0] = 0ull;
     gsync();
-    for (int k = 2; k <= np2; k <<= 1) {                         // ascending bitonic sort, keys distinct
+    for (int k = 2; k <= (nch > 1 ? np2 : 1); k <<= 1) {         // ascending bitonic sort, keys distinct
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = t; i < (np2 >> 1); i += tpc) {
                 const int ix = ((i & ~(j - 1)) << 1) | (i & (j - 1));
