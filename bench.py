@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
     ap.add_argument("--serving-slots", type=int, default=2000)
+    ap.add_argument("--serving-streams", type=int, default=8)
     return ap.parse_args()
 
 
@@ -333,11 +334,11 @@ def measure_batched(dev, flush) -> dict:
     return out
 
 
-def measure_serving(dev, n_slots: int) -> dict:
+def measure_serving(dev, n_slots: int, nstreams: int = 8) -> dict:
     """Open-loop serving: Poisson job arrivals (mean 4 per 0.5 ms slot); a job
     is one cell's slot, 3276 subcarriers x 14 symbols, K in {4, 8, 12, 16},
     M = 16, Q in {16, 64, 256}, n = 64, iid channels. Jobs are dispatched at
-    their arrival times round-robin over 4 streams (a plan per job type and
+    their arrival times round-robin over `nstreams` streams (a plan per job type and
     stream); latency = GPU completion - arrival, on one clock through a
     reference event. Inputs are one draw per job type, reused by its jobs."""
     import numpy as np
@@ -346,7 +347,6 @@ def measure_serving(dev, n_slots: int) -> dict:
     import paper_2602_12098_gb300 as vp
     from paper_2602_12098_gb300 import workloads as W
     jobs = W.poisson_jobs(n_slots)
-    nstreams = 4
     streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
     types = sorted({(j.K, j.M, j.qam, j.n_paths) for j in jobs})
     bufs = {}
@@ -550,7 +550,7 @@ def run_gpu(args):
     if ws == 1 and not args.no_batched:
         line["batched"] = measure_batched(dev, flush)
     if ws == 1 and not args.no_serving:
-        line["serving"] = measure_serving(dev, args.serving_slots)
+        line["serving"] = measure_serving(dev, args.serving_slots, args.serving_streams)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
