@@ -212,6 +212,47 @@ void orc_rank9(double sr, double si, int order[9])
     }
 }
 
+/* Region-LUT DEMAP (Section III-A-2: the effective point's position relative
+ * to its nearest lattice point addresses a table of neighbour orders). Reading:
+ * the nearest alphabet point n0 (clamped rounding, halves to the smaller
+ * value) and the octant of d = s_hat - n0 (sign of d.re, sign of d.im,
+ * |d.re| > |d.im|) select one of 9 x 8 regions; the region's list is the
+ * exact distance order of the 9 alphabet points seen from the octant's
+ * centroid n0 + (+-1/3, +-1/6) (x-dominant) or n0 + (+-1/6, +-1/3), ties to the
+ * smaller alphabet index. Distances are compared exactly in sixths. */
+static int lut_region(double sr, double si)
+{
+    const int nr = (sr > 0.5) - (sr <= -0.5), ni = (si > 0.5) - (si <= -0.5);
+    const double dr = sr - nr, di = si - ni;
+    const int oct = (dr > 0.0) | ((di > 0.0) << 1) | ((fabs(dr) > fabs(di)) << 2);
+    return ((nr + 1) * 3 + (ni + 1)) * 8 + oct;
+}
+
+void orc_lut_order(int region, int order[9])
+{
+    const int cell = region / 8, oct = region % 8;
+    const int nr = cell / 3 - 1, ni = cell % 3 - 1;
+    const int big = 2, small = 1;                 /* centroid offsets in sixths */
+    const int xr = (oct >> 2) ? big : small, xi = (oct >> 2) ? small : big;
+    const int pr = 6 * nr + ((oct & 1) ? xr : -xr), pi = 6 * ni + ((oct & 2) ? xi : -xi);
+    long d[9];
+    for (int a = 0; a < 9; a++) {
+        const int tr = a / 3 - 1, ti = a % 3 - 1;
+        d[a] = (long)(6 * tr - pr) * (6 * tr - pr) + (long)(6 * ti - pi) * (6 * ti - pi);
+        order[a] = a;
+    }
+    for (int i = 1; i < 9; i++) {                 /* insertion sort on (d, a) */
+        int a = order[i], j = i - 1;
+        while (j >= 0 && (d[order[j]] > d[a] || (d[order[j]] == d[a] && order[j] > a))) {
+            order[j + 1] = order[j];
+            j--;
+        }
+        order[j + 1] = a;
+    }
+}
+
+void orc_rank9_lut(double sr, double si, int order[9]) { orc_lut_order(lut_region(sr, si), order); }
+
 /* ------------------------------------------------------------------------ */
 /* Parallel post-processing of Alg. 2 for one data vector:
  *   for every candidate k: t^(k) = DEMAP(p^(k)), level K first, with the
@@ -224,6 +265,13 @@ void orc_rank9(double sr, double si, int order[9])
 void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int Mq,
                        const double* v_level, double tau, int n, const uint64_t* codes,
                        int* t_level, double* gamma, double* x, int* best, double* d_all)
+{
+    orc_search_vector_demap(K, M, Rt, Qbar, Mq, v_level, tau, n, codes, 0, t_level, gamma, x, best, d_all);
+}
+
+void orc_search_vector_demap(int K, int M, const double* Rt, const double* Qbar, int Mq,
+                             const double* v_level, double tau, int n, const uint64_t* codes, int demap,
+                             int* t_level, double* gamma, double* x, int* best, double* d_all)
 {
     int* t = (int*)malloc(sizeof(int) * 2 * K);
     int* tbest = (int*)calloc((size_t)2 * K, sizeof(int));
@@ -247,7 +295,8 @@ void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int M
                     num -= ld(Rt, l * K + m) * tau * (t[2 * m] + I * t[2 * m + 1]);
                 cplx sh = num / (ld(Rt, l * K + l) * tau);
                 int order[9];
-                orc_rank9(creal(sh), cimag(sh), order);
+                if (demap) orc_rank9_lut(creal(sh), cimag(sh), order);
+                else orc_rank9(creal(sh), cimag(sh), order);
                 int q = (int)((code >> (4 * l)) & 15u);
                 int a = order[q];
                 t[2 * l] = a / 3 - 1;
@@ -287,7 +336,7 @@ void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int M
 /* Whole pipeline over channels x vectors (Alg. 2 end to end). lambda > 0 is
  * the Tikhonov-regularised form: Hbar = [H lambda*I], Qbar has M+K columns,
  * and x is the first M entries of w / sqrt(gamma) with gamma = ||w||^2. */
-static void precode_channel(int K, int M, int qam, double tau, double lambda, int n_paths,
+static void precode_channel(int K, int M, int qam, double tau, double lambda, int demap, int n_paths,
                             const float* Hc, int v0, int v1, const uint8_t* sym_idx,
                             double* x, int8_t* l, double* gamma, int32_t* best, uint8_t* status)
 {
@@ -327,7 +376,7 @@ static void precode_channel(int K, int M, int qam, double tau, double lambda, in
         for (int lev = 0; lev < K; lev++)
             orc_qam_point(qam, sym_idx[(size_t)vi * K + ul[lev]], &v[2 * lev], &v[2 * lev + 1]);
         int kb;
-        orc_search_vector(K, M, Rt, Q, Mq, v, tau, np, codes, t, &gamma[vi], xv, &kb, NULL);
+        orc_search_vector_demap(K, M, Rt, Q, Mq, v, tau, np, codes, demap, t, &gamma[vi], xv, &kb, NULL);
         best[vi] = kb;
         for (int lev = 0; lev < K; lev++) {     /* l = -t, back to user order */
             lv[2 * ul[lev]] = (int8_t)(-t[2 * lev]);
@@ -337,7 +386,7 @@ static void precode_channel(int K, int M, int qam, double tau, double lambda, in
     free(H); free(R); free(Rt); free(Q); free(wgt); free(v); free(ul); free(t); free(codes);
 }
 
-int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int n_paths, int C,
+int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int demap, int n_paths, int C,
                       const float* H, const int32_t* vec_off, const uint8_t* sym_idx,
                       double* x, int8_t* l, double* gamma, int32_t* best,
                       uint8_t* status, int nthreads)
@@ -349,7 +398,7 @@ int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int n_pa
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (int c = 0; c < C; c++)
-        precode_channel(K, M, qam, tau, lambda, n_paths, H + (size_t)c * 2 * K * M,
+        precode_channel(K, M, qam, tau, lambda, demap, n_paths, H + (size_t)c * 2 * K * M,
                         vec_off[c], vec_off[c + 1], sym_idx, x, l, gamma, best, &status[c]);
     return 0;
 }

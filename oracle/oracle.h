@@ -76,6 +76,17 @@ int orc_mop_kbest(int K, const double* w, int n, uint64_t* codes, double* metric
  * exact-ranking reading of the neighbour ordering). */
 void orc_rank9(double sr, double si, int order[9]);
 
+/* Region-LUT DEMAP, the paper's table-driven alternative (Section III-A-2,
+ * "DEMAP" of Alg. 2). Reading: region = nearest alphabet point n0 (3 x 3) x
+ * octant of s_hat - n0 (signs, |re| > |im|), 72 regions; each region's list is
+ * the exact distance order from the octant centroid n0 + (+-1/3, +-1/6) or
+ * n0 + (+-1/6, +-1/3), ties to the smaller alphabet index.
+ *   orc_lut_order   the list of region r (0..71): r = ((n0r+1)*3 + n0i+1)*8 +
+ *                   [d.re > 0] + 2 [d.im > 0] + 4 [|d.re| > |d.im|]
+ *   orc_rank9_lut   the list for the effective point (sr, si) */
+void orc_lut_order(int region, int order[9]);
+void orc_rank9_lut(double sr, double si, int order[9]);
+
 /* Parallel post-processing of Alg. 2 for one data vector, plus the zero
  * perturbation as candidate 0.
  *   Rt           K x K upper, level order (Rtilde)
@@ -92,12 +103,17 @@ void orc_rank9(double sr, double si, int order[9]);
 void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int Mq,
                        const double* v_level, double tau, int n, const uint64_t* codes,
                        int* t_level, double* gamma, double* x, int* best, double* d_all);
+/* The same with the DEMAP chosen: demap 0 = exact ranking, 1 = region LUT. */
+void orc_search_vector_demap(int K, int M, const double* Rt, const double* Qbar, int Mq,
+                             const double* v_level, double tau, int n, const uint64_t* codes, int demap,
+                             int* t_level, double* gamma, double* x, int* best, double* d_all);
 
 /* Whole pipeline over a batch of channels, as the GPU library computes it.
  *   lambda     Tikhonov parameter of Alg. 2 "Regularize & factorize"
  *              (0: the plain sorted RQ, needs M >= K); with lambda > 0,
  *              gamma = ||w||^2 over all M+K entries of w = Qbar^H Rt (v - tau t)
  *              and x = the first M entries of w / sqrt(gamma)
+ *   demap      0: exact ranking (orc_rank9); 1: region LUT (orc_rank9_lut)
  *   H          complex64 [C][K][M] as float pairs (the GPU's own input)
  *   vec_off    [C+1] vector ranges per channel (channel c owns vectors
  *              vec_off[c] .. vec_off[c+1]-1)
@@ -106,7 +122,7 @@ void orc_search_vector(int K, int M, const double* Rt, const double* Qbar, int M
  * in user order, gamma [V], best [V]; per channel: status [C].
  * Channels whose status is nonzero get zero outputs.
  * nthreads > 1 runs channels in parallel (OpenMP), when built with it. */
-int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int n_paths, int C,
+int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int demap, int n_paths, int C,
                       const float* H, const int32_t* vec_off, const uint8_t* sym_idx,
                       double* x, int8_t* l, double* gamma, int32_t* best,
                       uint8_t* status, int nthreads);

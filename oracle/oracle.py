@@ -62,10 +62,13 @@ def lib():
             L.orc_mop_kbest.argtypes = [ctypes.c_int, dp, ctypes.c_int, u64p, dp]
             L.orc_mop_kbest.restype = ctypes.c_int
             L.orc_rank9.argtypes = [ctypes.c_double, ctypes.c_double, ip]
+            L.orc_rank9_lut.argtypes = [ctypes.c_double, ctypes.c_double, ip]
+            L.orc_lut_order.argtypes = [ctypes.c_int, ip]
             L.orc_search_vector.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp,
                                             ctypes.c_double, ctypes.c_int, u64p, ip, dp, dp, ip, dp]
             L.orc_precode_batch.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                             ctypes.c_double, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 8
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                            + [ctypes.c_void_p] * 8
                                             + [ctypes.c_int])
             L.orc_precode_batch.restype = ctypes.c_int
             L.orc_brute_min.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ip]
@@ -134,6 +137,20 @@ def mop_kbest(w, n: int):
     if got < 0:
         raise ValueError("bad MoP arguments")
     return codes[:got], met[:got]
+
+
+def rank9_lut(s_hat: complex) -> np.ndarray:
+    """Region-LUT DEMAP order (alphabet indices) for the effective point."""
+    order = np.zeros(9, dtype=np.intc)
+    lib().orc_rank9_lut(float(np.real(s_hat)), float(np.imag(s_hat)), _p(order, ctypes.c_int))
+    return order
+
+
+def lut_order(region: int) -> np.ndarray:
+    """The neighbour list of LUT region 0..71."""
+    order = np.zeros(9, dtype=np.intc)
+    lib().orc_lut_order(int(region), _p(order, ctypes.c_int))
+    return order
 
 
 def rank9(s_hat: complex) -> np.ndarray:
@@ -214,7 +231,7 @@ def factor_channel(H, n_paths: int, lam: float = 0.0):
 
 
 def precode_batch(H, sym_idx, vec_off, qam: int, n_paths: int, tau: float | None = None,
-                  nthreads: int = 1, lam: float = 0.0):
+                  nthreads: int = 1, lam: float = 0.0, demap: str = "exact"):
     """Whole pipeline (factor + MoP + search + x) over channels.
 
     H        complex64 [C, K, M]
@@ -234,7 +251,7 @@ def precode_batch(H, sym_idx, vec_off, qam: int, n_paths: int, tau: float | None
     gamma = np.zeros(V, dtype=np.float64)
     best = np.zeros(V, dtype=np.int32)
     status = np.zeros(C, dtype=np.uint8)
-    rc = lib().orc_precode_batch(K, M, qam, tau, float(lam), int(n_paths), C,
+    rc = lib().orc_precode_batch(K, M, qam, tau, float(lam), {"exact": 0, "lut": 1}[demap], int(n_paths), C,
                                  H.ctypes.data, vec_off.ctypes.data, sym_idx.ctypes.data,
                                  x.ctypes.data, l.ctypes.data, gamma.ctypes.data,
                                  best.ctypes.data, status.ctypes.data, int(nthreads))
