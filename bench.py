@@ -334,6 +334,48 @@ def measure_batched(dev, flush) -> dict:
     return out
 
 
+def measure_lut(dev, b, w, flush, steps: int) -> dict:
+    """The same slot with the region-LUT DEMAP (VP_DEMAP_LUT): vp_precode time
+    and the gamma it reaches against the exact ranking (same paths)."""
+    import numpy as np
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    C, K, M = b.H.shape
+    V, S = b.sym.shape[0], w.symbols
+    stream = torch.cuda.current_stream()
+    H = torch.from_numpy(b.H).to(dev)
+    sym = torch.from_numpy(b.sym).to(dev)
+    out = {}
+    g = {}
+    for name, mode in (("exact", vp.VP_DEMAP_EXACT), ("lut", vp.VP_DEMAP_LUT)):
+        x = torch.empty((V, M), dtype=torch.complex64, device=dev)
+        l = torch.empty((V, K, 2), dtype=torch.int8, device=dev)
+        gam = torch.empty((V,), dtype=torch.float32, device=dev)
+        with vp.Plan(K, M, w.qam, w.n_paths, demap=mode) as plan:
+            vp.vp_factorize(plan.handle, H, C, stream=stream)
+            for _ in range(3):
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, gam, stream=stream)
+            ts = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, gam, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        out[name + "_precode_ms"] = statistics.median(ts)
+        g[name] = gam.cpu().numpy().astype(np.float64)
+    m = g["exact"] > 0
+    r = g["lut"][m] / g["exact"][m]
+    out["search_speedup"] = out["exact_precode_ms"] / out["lut_precode_ms"]
+    out["gamma_ratio_mean"] = float(r.mean())
+    out["gamma_ratio_p99"] = float(np.percentile(r, 99))
+    out["note"] = "VP_DEMAP_LUT (region lookup, Section III-A-2) vs the exact ranking on the same slot and paths"
+    return out
+
+
 def measure_serving(dev, n_slots: int, nstreams: int = 8) -> dict:
     """Open-loop serving: Poisson job arrivals (mean 4 per 0.5 ms slot); a job
     is one cell's slot, 3276 subcarriers x 14 symbols, K in {4, 8, 12, 16},
@@ -548,6 +590,7 @@ def run_gpu(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches[0], "clocks": clocks}
     plan.close()
     if ws == 1 and not args.no_batched:
+        line["demap_lut"] = measure_lut(dev, b, w, flush, min(args.steps, 100))
         line["batched"] = measure_batched(dev, flush)
     if ws == 1 and not args.no_serving:
         line["serving"] = measure_serving(dev, args.serving_slots, args.serving_streams)

@@ -109,6 +109,21 @@ vp_status vp_plan_set_fp64_threshold(vp_plan* plan, float kappa_hat);
  */
 vp_status vp_plan_set_lambda(vp_plan* plan, float lambda);
 
+/*
+ * DEMAP of Alg. 2 (the p_l-th point around the effective point of Eq. 17):
+ *   VP_DEMAP_EXACT  exact ranking by distance, ties to the smaller alphabet
+ *                   index (the default)
+ *   VP_DEMAP_LUT    the region lookup of Section III-A-2: the nearest alphabet
+ *                   point (3 x 3) and the octant of the offset from it select
+ *                   one of 72 stored orders, each the exact order seen from
+ *                   the octant's centroid (n0 + (+-1/3, +-1/6) or
+ *                   n0 + (+-1/6, +-1/3)). An approximation: a path's point can
+ *                   differ from the exact ranking's away from the centroid.
+ * Takes effect at the next vp_precode. Other values are invalid.
+ */
+typedef enum { VP_DEMAP_EXACT = 0, VP_DEMAP_LUT = 1 } vp_demap;
+vp_status vp_plan_set_demap(vp_plan* plan, int demap);
+
 /* Free the plan and its device state. Synchronises the device first so that
  * no enqueued work still reads the state. NULL is accepted. */
 vp_status vp_plan_destroy(vp_plan* plan);

@@ -136,6 +136,13 @@ vp_status vp_plan_set_lambda(vp_plan* p, float lambda)
     return VP_OK;
 }
 
+vp_status vp_plan_set_demap(vp_plan* p, int demap)
+{
+    if (!p || (demap != VP_DEMAP_EXACT && demap != VP_DEMAP_LUT)) return VP_ERR_INVALID_ARG;
+    p->demap = demap;
+    return VP_OK;
+}
+
 vp_status vp_plan_destroy(vp_plan* p)
 {
     if (!p) return VP_OK;

@@ -39,6 +39,7 @@ struct SearchArgs {
     const BatchProblem* probs;
     const int* ids;
     int KM, NP;
+    int demap;       // VP_DEMAP_* (plan launches)
 };
 
 // DEMAP selection: the q-th (0-based) nearest point t of {-1,0,1}+j{-1,0,1}
@@ -127,17 +128,63 @@ __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, 
 // One level of the descent for a lane's candidate: DEMAP selection of the
 // digit's point around r'_lv, PED update, the chosen t recorded as a 4-bit
 // code, and the column update r'_m -= U~_m,lv t for m < lv.
-template <int KT>
+// Region-LUT DEMAP: nearest alphabet point n0 (clamped rounding, halves to
+// the smaller value) and the octant of d = c - n0 pick one of 72 regions; the
+// region's list (9 alphabet indices, 4 bits each) is the exact distance order
+// from the octant centroid, built once per block by build_lut.
+__device__ __forceinline__ void select_lut(float cx, float cy, int q, const uint64_t* lut, int& tr, int& ti)
+{
+    const int nx = (cx > 0.5f) - (cx <= -0.5f), ny = (cy > 0.5f) - (cy <= -0.5f);
+    const float dx = cx - (float)nx, dy = cy - (float)ny;
+    const int oct = (dx > 0.f) | ((dy > 0.f) << 1) | ((fabsf(dx) > fabsf(dy)) << 2);
+    const int a = (int)(lut[((nx + 1) * 3 + (ny + 1)) * 8 + oct] >> (4 * q)) & 15;
+    tr = ((a * 11) >> 5) - 1;                        // a / 3 for a <= 8
+    ti = a - 3 * (tr + 1) - 1;
+}
+
+// The 72 region lists: distances from the octant centroid n0 + (+-1/3, +-1/6)
+// (|d.re| > |d.im|) or n0 + (+-1/6, +-1/3), compared exactly in sixths, ties to
+// the smaller alphabet index a = 3 (tr + 1) + (ti + 1).
+__device__ void build_lut(uint64_t* lut)
+{
+    for (int rg = threadIdx.x; rg < 72; rg += blockDim.x) {
+        const int cell = rg >> 3, oct = rg & 7;
+        const int cx = 6 * (cell / 3 - 1) + ((oct & 1) ? 1 : -1) * ((oct & 4) ? 2 : 1);
+        const int cy = 6 * (cell % 3 - 1) + ((oct & 2) ? 1 : -1) * ((oct & 4) ? 1 : 2);
+        int key[9];
+        for (int a = 0; a < 9; ++a) {
+            const int ex = 6 * (a / 3 - 1) - cx, ey = 6 * (a % 3 - 1) - cy;
+            key[a] = (ex * ex + ey * ey) * 16 + a;          // distance, then index
+        }
+        uint64_t word = 0;
+        for (int q = 0; q < 9; ++q) {                       // q-th smallest key
+            int best = 0x7fffffff;
+            for (int a = 0; a < 9; ++a) {
+                int rankless = 0;
+                for (int b = 0; b < 9; ++b) rankless += key[b] < key[a];
+                if (rankless == q) best = a;
+            }
+            word |= (uint64_t)best << (4 * q);
+        }
+        lut[rg] = word;
+    }
+}
+
+template <int KT, bool LUT>
 __device__ __forceinline__ void level_step(int lv, const float4* utp, const float* wv, uint32_t cw0, uint32_t cw1,
-                                           uint32_t mq0, uint32_t mq1, float2 (&r)[KT], float& ped, uint32_t& lc0,
-                                           uint32_t& lc1)
+                                           uint32_t mq0, uint32_t mq1, const uint64_t* lut, float2 (&r)[KT],
+                                           float& ped, uint32_t& lc0, uint32_t& lc1)
 {
     const int sh = 4 * (lv & 7);
     const int q = (int)(((lv < 8) ? cw0 : cw1) >> sh) & 15;
-    const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
     const float cx = r[lv].x, cy = r[lv].y;
     int tr, ti;
-    select_point(cx, cy, q, mql, tr, ti);
+    if (LUT) {
+        select_lut(cx, cy, q, lut, tr, ti);
+    } else {
+        const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
+        select_point(cx, cy, q, mql, tr, ti);
+    }
     const float ftr = (float)tr, fti = (float)ti;
     const float dx = cx - ftr, dy = cy - fti;
     ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
@@ -167,7 +214,7 @@ __host__ __device__ inline int take16(int& o, int bytes)
 
 // Shared-memory layout of one search block (byte offsets, 16-byte aligned).
 struct SearchSmem {
-    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, scrl, scrp, wv, ulv, meta, total;
+    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, lut, scrl, scrp, wv, ulv, meta, total;
 };
 
 __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW)
@@ -188,6 +235,7 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
     s.wv = take16(o, 4 * KT);
     s.ulv = take16(o, 4 * KT);
     s.meta = take16(o, 4 * NP);
+    s.lut = take16(o, 8 * 72);
     s.total = o;
     return s;
 }
@@ -200,7 +248,7 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
 // then continues from its prefix's state through the remaining levels. The
 // arithmetic per path is the same as a full descent, so results are
 // identical; the shared levels are the ones with the most column updates.
-template <int KT, bool BATCH>
+template <int KT, bool BATCH, bool LUT>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -251,6 +299,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     float* wv = reinterpret_cast<float*>(smraw + L.wv);            // [KT]
     int* ulv = reinterpret_cast<int*>(smraw + L.ulv);              // [KT]
     uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + L.meta);  // [n] MoP rank | prefix << 16
+    uint64_t* lut = reinterpret_cast<uint64_t*>(smraw + L.lut);    // [72] region lists (LUT DEMAP)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
@@ -291,6 +340,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     const int NPF = T > 0 ? hdr.y : 1;
     const uint64_t amq = (uint64_t)(uint32_t)hdr.z | ((uint64_t)(uint32_t)hdr.w << 32);
     if (T == 0 && threadIdx.x == 0) pcode[0] = 0ull;
+    if (LUT) build_lut(lut);
     __syncthreads();
 
     float2* bw = bvec + warp * KT;
@@ -328,7 +378,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
             for (int lv = KT - 1; lv >= kLo; --lv) {
                 if (lv >= KT - T)
-                    level_step<KT>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), r, ped, lc0, lc1);
+                    level_step<KT, LUT>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, r, ped,
+                                        lc0, lc1);
             }
             if (lane < NPF) {
 #pragma unroll
@@ -361,7 +412,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
             for (int lv = KT - 1; lv >= 0; --lv) {
                 if (lv < KB)
-                    level_step<KT>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), r, ped, lc0, lc1);
+                    level_step<KT, LUT>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, r, ped,
+                                        lc0, lc1);
             }
             if (vld && (ped < bp || (ped == bp && rk < brk))) { bp = ped; brk = rk; blc0 = lc0; blc1 = lc1; }
         }
@@ -417,30 +469,29 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     }
 }
 
+template <int KT, bool BATCH, bool LUT>
+cudaError_t launch_one(const SearchArgs& a, int C, int threads, size_t sh, cudaStream_t s)
+{
+    static size_t attr = 0;
+    if (sh > 40 * 1024 && sh > attr) {
+        cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, BATCH, LUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        attr = sh;
+    }
+    search_kernel<KT, BATCH, LUT><<<C, threads, sh, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int KT>
 cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
 {
     const int NW = threads / 32;
     const int KM = a.probs ? a.KM : a.K * a.Mp, NP = a.probs ? a.NP : a.n;
     const size_t sh = (size_t)search_smem(KT, KM, NP, NW).total;
-    if (a.probs) {
-        static size_t attr = 0;
-        if (sh > 40 * 1024 && sh > attr) {
-            cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-            if (e != cudaSuccess) return e;
-            attr = sh;
-        }
-        search_kernel<KT, true><<<C, threads, sh, s>>>(a);
-    } else {
-        static size_t attr = 0;
-        if (sh > 40 * 1024 && sh > attr) {
-            cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-            if (e != cudaSuccess) return e;
-            attr = sh;
-        }
-        search_kernel<KT, false><<<C, threads, sh, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (a.probs) return launch_one<KT, true, false>(a, C, threads, sh, s);
+    if (a.demap == VP_DEMAP_LUT) return launch_one<KT, false, true>(a, C, threads, sh, s);
+    return launch_one<KT, false, false>(a, C, threads, sh, s);
 }
 
 }  // namespace
@@ -460,6 +511,7 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     a.K = p->K;
     a.M = p->M;
     a.Mp = p_rows(p);
+    a.demap = p->demap;
     a.n = p->n_paths;
     a.nch = n_chunks(p->n_paths);
     int m = 1;

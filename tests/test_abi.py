@@ -120,3 +120,16 @@ def test_overloaded_plan_needs_lambda():
         vp.vp_plan_set_lambda(h, 0.0)
     finally:
         vp.vp_plan_destroy(h)
+
+
+def test_demap_option_validation():
+    h = vp.vp_plan_create(4, 4, 16, 16)
+    try:
+        vp.vp_plan_set_demap(h, vp.VP_DEMAP_LUT)
+        vp.vp_plan_set_demap(h, vp.VP_DEMAP_EXACT)
+        for bad in (-1, 2, 7):
+            with pytest.raises(vp.VPError) as e:
+                vp.vp_plan_set_demap(h, bad)
+            assert e.value.code == 1
+    finally:
+        vp.vp_plan_destroy(h)
