@@ -553,7 +553,8 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(b.H.nbytes + b.sym.nbytes),
                "d2h_bytes_per_step": int(V * M * 8 + V * K * 2 + V * 4),
                "p50_slot_ms": 1e3 * statistics.median(ts),
-               "api": "vp_run_slot_host (H2D copies, vp_factorize, vp_precode, D2H copies, stream sync)"}
+               "api": "vp_run_slot_host (H2D copies of H and symbols, vp_factorize, vp_precode writing x, l, gamma "
+                      "into the pinned host buffers over the C2C link, stream sync)"}
 
     # roofline of the dominant kernel (the search), ALU-bound FP32
     import json as _json

@@ -174,10 +174,12 @@ vp_status vp_get_paths(vp_plan* plan, uint64_t* codes, void* stream);
 
 /*
  * One whole slot from HOST buffers: copies H and sym_idx to the device,
- * runs vp_factorize and vp_precode (S vectors per channel), copies x, l and
- * gamma back, and waits for the stream. Host buffers should be pinned
- * (cudaHostAlloc / cudaHostRegister) for asynchronous copies; pageable
- * memory works but copies synchronously.
+ * runs vp_factorize and vp_precode (S vectors per channel), returns x, l and
+ * gamma, and waits for the stream. Outputs in page-locked, mapped memory
+ * (cudaHostAlloc, or cudaHostRegister with cudaHostRegisterMapped) are
+ * written by the search kernel in place (on Grace systems over NVLink-C2C);
+ * others are copied back. Host buffers should be pinned for asynchronous
+ * copies; pageable memory works but copies synchronously.
  *   H_host      HOST complex64 [C][K][M]
  *   sym_host    HOST uint8 [C*S][K]
  *   x_host      HOST complex64 [C*S][M]

@@ -85,6 +85,25 @@ vp_status ensure_buf(T** p, size_t* have, size_t need)
     return VP_OK;
 }
 
+// Device address of page-locked host memory that the GPU can read and write
+// in place (over NVLink-C2C on Grace systems), or null (pageable memory, or
+// the mapping is not available).
+void* mapped(const void* hp)
+{
+    if (!hp) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, hp) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, const_cast<void*>(hp), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return dp;
+}
+
 }  // namespace
 
 extern "C" {
@@ -215,22 +234,30 @@ vp_status vp_run_slot_host(vp_plan* p, const void* H_host, int C, const uint8_t*
     const size_t hb = sizeof(float2) * (size_t)C * p->K * p->M;
     const size_t sb = V * p->K, xb = sizeof(float2) * V * p->M, lb = V * p->K * 2, gb = sizeof(float) * V;
     vp_status st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = ensure_buf(&p->h_H, &p->h_H_bytes, hb)) != VP_OK) return st;
     if ((st = ensure_buf(&p->h_sym, &p->h_sym_bytes, sb + 1)) != VP_OK) return st;
     if ((st = ensure_buf(&p->h_x, &p->h_x_bytes, xb + 1)) != VP_OK) return st;
     if ((st = ensure_buf(&p->h_l, &p->h_l_bytes, lb + 1)) != VP_OK) return st;
     if ((st = ensure_buf(&p->h_g, &p->h_g_bytes, gb + 1)) != VP_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemcpyAsync(p->h_H, H_host, hb, cudaMemcpyHostToDevice, s) != cudaSuccess) return VP_ERR_CUDA;
     if (sb && cudaMemcpyAsync(p->h_sym, sym_host, sb, cudaMemcpyHostToDevice, s) != cudaSuccess) return VP_ERR_CUDA;
     if ((st = vp_factorize(p, p->h_H, C, nullptr, nullptr, nullptr, nullptr, stream)) != VP_OK) return st;
     const int nf = p->last_launches;
-    if ((st = vp_precode(p, p->h_sym, S, nullptr, (int)V, p->h_x, p->h_l, p->h_g, stream)) != VP_OK) return st;
+    // page-locked, mapped output buffers are written by the search kernel in
+    // place (over NVLink-C2C on Grace systems), saving the copies back
+    void* xd = mapped(x_host);
+    void* ld = mapped(l_host);
+    void* gd = mapped(gamma_host);
+    if ((st = vp_precode(p, p->h_sym, S, nullptr, (int)V, xd ? xd : p->h_x, ld ? static_cast<int8_t*>(ld) : p->h_l,
+                         gd ? static_cast<float*>(gd) : p->h_g, stream)) != VP_OK)
+        return st;
     p->last_launches += nf;
-    if (xb && cudaMemcpyAsync(x_host, p->h_x, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return VP_ERR_CUDA;
-    if (l_host && lb && cudaMemcpyAsync(l_host, p->h_l, lb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (!xd && xb && cudaMemcpyAsync(x_host, p->h_x, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return VP_ERR_CUDA;
-    if (gamma_host && gb && cudaMemcpyAsync(gamma_host, p->h_g, gb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (l_host && !ld && lb && cudaMemcpyAsync(l_host, p->h_l, lb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return VP_ERR_CUDA;
+    if (gamma_host && !gd && gb && cudaMemcpyAsync(gamma_host, p->h_g, gb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return VP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return VP_ERR_CUDA;
     return VP_OK;
