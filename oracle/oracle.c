@@ -333,10 +333,111 @@ void orc_search_vector_demap(int K, int M, const double* Rt, const double* Qbar,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Fixed-point form of the search (the accelerator's datapath of Section IV:
+ * signed words of `word` bits, `frac` of them fractional; the paper keeps 16
+ * bits and studies 8..13 fractional bits). Reading: the quantities held in
+ * that format are the ones the descent updates, the level residuals in units
+ * of tau, r'_m = (s_m + sum_{k>m} Ut_mk (s_k - tau t_k)) / tau, and the
+ * normalised entries Ut_mk = Rt_mk / Rt_mm they are updated with. Each word
+ * is the nearest multiple of 2^-frac (halves to even), saturated to
+ * +-(2^(word-1) - 1) 2^-frac per real component. The entries are rounded
+ * first; the starting residual b'_m = (s_m + sum_{k>m} Utq_mk s_k) / tau is
+ * formed from them with a wide accumulator (exact: small odd integers times
+ * words) and rounded once; every column update r'_m <- r'_m - Utq_ml t_l
+ * saturates (exact integer arithmetic).
+ * DEMAP ranks the quantised point; the PED sum_l |Rt_ll|^2 tau^2 |r'_l - t_l|^2
+ * and the argmin are exact, and gamma and x are computed exactly for the chosen
+ * t. */
+static double qfix(double v, double scale, double lim)
+{
+    double q = nearbyint(v * scale);           /* round-half-even in the default mode */
+    if (q > lim) q = lim;
+    if (q < -lim) q = -lim;
+    return q / scale;
+}
+
+static double clampd(double v, double lim) { return v > lim ? lim : (v < -lim ? -lim : v); }
+
+void orc_search_vector_fixed(int K, int M, const double* Rt, const double* Qbar, int Mq,
+                             const double* v_level, double tau, int n, const uint64_t* codes, int demap,
+                             int frac, int word, int* t_level, double* gamma, double* x, int* best)
+{
+    const double scale = ldexp(1.0, frac), ilim = ldexp(1.0, word - 1) - 1.0, lim = ilim / scale;
+    cplx* ut = (cplx*)malloc(sizeof(cplx) * K * K);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * K);
+    cplx* r = (cplx*)malloc(sizeof(cplx) * K);
+    double* wt = (double*)malloc(sizeof(double) * K);
+    int* t = (int*)malloc(sizeof(int) * 2 * K);
+    int* tbest = (int*)calloc((size_t)2 * K, sizeof(int));
+    for (int m = 0; m < K; m++) {
+        const cplx d = ld(Rt, m * K + m);
+        wt[m] = creal(d * conj(d)) * tau * tau;
+        cplx acc = ld(v_level, m);
+        for (int k = m + 1; k < K; k++) {
+            const cplx u = ld(Rt, m * K + k) / d;
+            ut[m * K + k] = qfix(creal(u), scale, ilim) + I * qfix(cimag(u), scale, ilim);
+            acc += ut[m * K + k] * ld(v_level, k);
+        }
+        acc /= tau;
+        b[m] = qfix(creal(acc), scale, ilim) + I * qfix(cimag(acc), scale, ilim);
+    }
+    double pbest = 0.0;                        /* candidate 0: t = 0 */
+    for (int m = 0; m < K; m++) pbest += wt[m] * creal(b[m] * conj(b[m]));
+    int kbest = 0;
+    for (int cand = 1; cand <= n; cand++) {
+        const uint64_t code = codes[cand - 1];
+        for (int m = 0; m < K; m++) r[m] = b[m];
+        double ped = 0.0;
+        for (int l = K - 1; l >= 0; l--) {
+            int order[9];
+            if (demap) orc_rank9_lut(creal(r[l]), cimag(r[l]), order);
+            else orc_rank9(creal(r[l]), cimag(r[l]), order);
+            const int a = order[(int)((code >> (4 * l)) & 15u)];
+            const int tr = a / 3 - 1, ti = a % 3 - 1;
+            t[2 * l] = tr;
+            t[2 * l + 1] = ti;
+            const cplx e = r[l] - (tr + I * ti);
+            ped += wt[l] * creal(e * conj(e));
+            for (int m = 0; m < l; m++) {
+                const cplx v = r[m] - ut[m * K + l] * (tr + I * ti);
+                r[m] = clampd(creal(v), lim) + I * clampd(cimag(v), lim);
+            }
+        }
+        if (ped < pbest) {
+            pbest = ped;
+            kbest = cand;
+            memcpy(tbest, t, sizeof(int) * 2 * K);
+        }
+    }
+    /* gamma and x for the chosen perturbation: w = Qbar^H Rt (v - tau t) */
+    cplx* z = (cplx*)malloc(sizeof(cplx) * K);
+    for (int l = 0; l < K; l++) {
+        cplx s = 0.0;
+        for (int m = l; m < K; m++)
+            s += ld(Rt, l * K + m) * (ld(v_level, m) - tau * (tbest[2 * m] + I * tbest[2 * m + 1]));
+        z[l] = s;
+    }
+    double d = 0.0;
+    cplx* w = (cplx*)malloc(sizeof(cplx) * Mq);
+    for (int c = 0; c < Mq; c++) {
+        cplx s = 0.0;
+        for (int l = 0; l < K; l++) s += conj(ld(Qbar, l * Mq + c)) * z[l];
+        w[c] = s;
+        d += creal(s * conj(s));
+    }
+    *gamma = d;
+    *best = kbest;
+    memcpy(t_level, tbest, sizeof(int) * 2 * K);
+    for (int c = 0; c < M; c++) st(x, c, w[c] / sqrt(d));
+    free(ut); free(b); free(r); free(wt); free(t); free(tbest); free(z); free(w);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Whole pipeline over channels x vectors (Alg. 2 end to end). lambda > 0 is
  * the Tikhonov-regularised form: Hbar = [H lambda*I], Qbar has M+K columns,
  * and x is the first M entries of w / sqrt(gamma) with gamma = ||w||^2. */
-static void precode_channel(int K, int M, int qam, double tau, double lambda, int demap, int n_paths,
+static void precode_channel(int K, int M, int qam, double tau, double lambda, int demap, int frac,
+                            int word, int n_paths,
                             const float* Hc, int v0, int v1, const uint8_t* sym_idx,
                             double* x, int8_t* l, double* gamma, int32_t* best, uint8_t* status)
 {
@@ -376,7 +477,9 @@ static void precode_channel(int K, int M, int qam, double tau, double lambda, in
         for (int lev = 0; lev < K; lev++)
             orc_qam_point(qam, sym_idx[(size_t)vi * K + ul[lev]], &v[2 * lev], &v[2 * lev + 1]);
         int kb;
-        orc_search_vector_demap(K, M, Rt, Q, Mq, v, tau, np, codes, demap, t, &gamma[vi], xv, &kb, NULL);
+        if (frac > 0)
+            orc_search_vector_fixed(K, M, Rt, Q, Mq, v, tau, np, codes, demap, frac, word, t, &gamma[vi], xv, &kb);
+        else orc_search_vector_demap(K, M, Rt, Q, Mq, v, tau, np, codes, demap, t, &gamma[vi], xv, &kb, NULL);
         best[vi] = kb;
         for (int lev = 0; lev < K; lev++) {     /* l = -t, back to user order */
             lv[2 * ul[lev]] = (int8_t)(-t[2 * lev]);
@@ -386,19 +489,21 @@ static void precode_channel(int K, int M, int qam, double tau, double lambda, in
     free(H); free(R); free(Rt); free(Q); free(wgt); free(v); free(ul); free(t); free(codes);
 }
 
-int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int demap, int n_paths, int C,
+int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int demap, int frac, int word,
+                      int n_paths, int C,
                       const float* H, const int32_t* vec_off, const uint8_t* sym_idx,
                       double* x, int8_t* l, double* gamma, int32_t* best,
                       uint8_t* status, int nthreads)
 {
     if (K < 1 || K > 16 || M < 1 || n_paths < 1 || C < 0 || !(lambda >= 0.0)) return -1;
     if (M < K && lambda == 0.0) return -1;   /* H H^H is singular without the regularisation */
+    if (frac < 0 || (frac > 0 && (word < 2 || word > 53 || frac > 52))) return -1;
     if (nthreads < 1) nthreads = 1;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (int c = 0; c < C; c++)
-        precode_channel(K, M, qam, tau, lambda, demap, n_paths, H + (size_t)c * 2 * K * M,
+        precode_channel(K, M, qam, tau, lambda, demap, frac, word, n_paths, H + (size_t)c * 2 * K * M,
                         vec_off[c], vec_off[c + 1], sym_idx, x, l, gamma, best, &status[c]);
     return 0;
 }

@@ -108,12 +108,27 @@ void orc_search_vector_demap(int K, int M, const double* Rt, const double* Qbar,
                              const double* v_level, double tau, int n, const uint64_t* codes, int demap,
                              int* t_level, double* gamma, double* x, int* best, double* d_all);
 
+/* Fixed-point search (Section IV's datapath: signed `word`-bit values with
+ * `frac` fractional bits; the accelerator uses 16 bits). The level residuals
+ * in units of tau and the normalised entries Rt_mk / Rt_mm are rounded half to
+ * even to multiples of 2^-frac and saturated to +-(2^(word-1) - 1) 2^-frac (the
+ * starting residuals formed from the rounded entries and rounded once), the
+ * residual updates saturate at every level, DEMAP (demap 0 exact, 1 region
+ * LUT) ranks the quantised point; the PEDs, the argmin, gamma and x are
+ * exact. */
+void orc_search_vector_fixed(int K, int M, const double* Rt, const double* Qbar, int Mq,
+                             const double* v_level, double tau, int n, const uint64_t* codes, int demap,
+                             int frac, int word, int* t_level, double* gamma, double* x, int* best);
+
 /* Whole pipeline over a batch of channels, as the GPU library computes it.
  *   lambda     Tikhonov parameter of Alg. 2 "Regularize & factorize"
  *              (0: the plain sorted RQ, needs M >= K); with lambda > 0,
  *              gamma = ||w||^2 over all M+K entries of w = Qbar^H Rt (v - tau t)
  *              and x = the first M entries of w / sqrt(gamma)
  *   demap      0: exact ranking (orc_rank9); 1: region LUT (orc_rank9_lut)
+ *   frac, word 0: floating-point search; frac > 0: the fixed-point search
+ *              (orc_search_vector_fixed) with `word`-bit values (2..53),
+ *              `frac` (1..52) of them fractional
  *   H          complex64 [C][K][M] as float pairs (the GPU's own input)
  *   vec_off    [C+1] vector ranges per channel (channel c owns vectors
  *              vec_off[c] .. vec_off[c+1]-1)
@@ -122,7 +137,8 @@ void orc_search_vector_demap(int K, int M, const double* Rt, const double* Qbar,
  * in user order, gamma [V], best [V]; per channel: status [C].
  * Channels whose status is nonzero get zero outputs.
  * nthreads > 1 runs channels in parallel (OpenMP), when built with it. */
-int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int demap, int n_paths, int C,
+int orc_precode_batch(int K, int M, int qam, double tau, double lambda, int demap, int frac, int word,
+                      int n_paths, int C,
                       const float* H, const int32_t* vec_off, const uint8_t* sym_idx,
                       double* x, int8_t* l, double* gamma, int32_t* best,
                       uint8_t* status, int nthreads);

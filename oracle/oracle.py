@@ -67,7 +67,8 @@ def lib():
             L.orc_search_vector.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp,
                                             ctypes.c_double, ctypes.c_int, u64p, ip, dp, dp, ip, dp]
             L.orc_precode_batch.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int]
                                             + [ctypes.c_void_p] * 8
                                             + [ctypes.c_int])
             L.orc_precode_batch.restype = ctypes.c_int
@@ -231,8 +232,12 @@ def factor_channel(H, n_paths: int, lam: float = 0.0):
 
 
 def precode_batch(H, sym_idx, vec_off, qam: int, n_paths: int, tau: float | None = None,
-                  nthreads: int = 1, lam: float = 0.0, demap: str = "exact"):
+                  nthreads: int = 1, lam: float = 0.0, demap: str = "exact", frac_bits: int = 0,
+                  word_bits: int = 16):
     """Whole pipeline (factor + MoP + search + x) over channels.
+
+    frac_bits > 0 runs the fixed-point search (Section IV) with word_bits-bit
+    values, frac_bits of them fractional; 0 is the floating-point search.
 
     H        complex64 [C, K, M]
     sym_idx  uint8 [V, K] (user order)
@@ -251,7 +256,8 @@ def precode_batch(H, sym_idx, vec_off, qam: int, n_paths: int, tau: float | None
     gamma = np.zeros(V, dtype=np.float64)
     best = np.zeros(V, dtype=np.int32)
     status = np.zeros(C, dtype=np.uint8)
-    rc = lib().orc_precode_batch(K, M, qam, tau, float(lam), {"exact": 0, "lut": 1}[demap], int(n_paths), C,
+    rc = lib().orc_precode_batch(K, M, qam, tau, float(lam), {"exact": 0, "lut": 1}[demap], int(frac_bits),
+                                 int(word_bits), int(n_paths), C,
                                  H.ctypes.data, vec_off.ctypes.data, sym_idx.ctypes.data,
                                  x.ctypes.data, l.ctypes.data, gamma.ctypes.data,
                                  best.ctypes.data, status.ctypes.data, int(nthreads))
