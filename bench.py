@@ -376,6 +376,55 @@ def measure_lut(dev, b, w, flush, steps: int) -> dict:
     return out
 
 
+def measure_fixed(dev, b, w, flush, steps: int, fracs=(8, 9, 10, 11, 12, 13)) -> dict:
+    """The word-length study (Section IV: 16-bit words, 8..13 fractional
+    bits): the same slot and factor with the fixed-point search; per F the
+    vp_precode time, the gamma it reaches against the floating-point search
+    and the share of vectors whose l differs from it."""
+    import numpy as np
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    C, K, M = b.H.shape
+    V, S = b.sym.shape[0], w.symbols
+    stream = torch.cuda.current_stream()
+    H = torch.from_numpy(b.H).to(dev)
+    sym = torch.from_numpy(b.sym).to(dev)
+    x = torch.empty((V, M), dtype=torch.complex64, device=dev)
+    l = torch.empty((V, K, 2), dtype=torch.int8, device=dev)
+    gam = torch.empty((V,), dtype=torch.float32, device=dev)
+    res = {}
+    with vp.Plan(K, M, w.qam, w.n_paths) as plan:
+        vp.vp_factorize(plan.handle, H, C, stream=stream)
+        for f in (0,) + tuple(fracs):
+            vp.vp_plan_set_fixed_point(plan.handle, f)
+            for _ in range(3):
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, gam, stream=stream)
+            ts = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, gam, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res[f] = (statistics.median(ts), gam.cpu().numpy().astype(np.float64), l.cpu().numpy())
+    g0, l0 = res[0][1], res[0][2]
+    m = g0 > 0
+    out = {"float_precode_ms": res[0][0], "by_frac_bits": {}}
+    for f in fracs:
+        ms, g, lf = res[f]
+        r = g[m] / g0[m]
+        out["by_frac_bits"][str(f)] = {
+            "precode_ms": ms, "gamma_ratio_mean": float(r.mean()), "gamma_ratio_p99": float(np.percentile(r, 99)),
+            "gamma_penalty_db": float(10 * np.log10(r.mean())),
+            "l_differs": float(np.mean(np.any(lf != l0, axis=(1, 2))))}
+    out["note"] = ("vp_plan_set_fixed_point (16-bit words, F fractional bits) vs the floating-point search "
+                   "on the same slot, factor and paths")
+    return out
+
+
 def measure_serving(dev, n_slots: int, nstreams: int = 8) -> dict:
     """Open-loop serving: Poisson job arrivals (mean 4 per 0.5 ms slot); a job
     is one cell's slot, 3276 subcarriers x 14 symbols, K in {4, 8, 12, 16},
@@ -592,6 +641,7 @@ def run_gpu(args):
     plan.close()
     if ws == 1 and not args.no_batched:
         line["demap_lut"] = measure_lut(dev, b, w, flush, min(args.steps, 100))
+        line["fixed_point"] = measure_fixed(dev, b, w, flush, min(args.steps, 20))
         line["batched"] = measure_batched(dev, flush)
     if ws == 1 and not args.no_serving:
         line["serving"] = measure_serving(dev, args.serving_slots, args.serving_streams)

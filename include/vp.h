@@ -124,6 +124,27 @@ vp_status vp_plan_set_lambda(vp_plan* plan, float lambda);
 typedef enum { VP_DEMAP_EXACT = 0, VP_DEMAP_LUT = 1 } vp_demap;
 vp_status vp_plan_set_demap(vp_plan* plan, int demap);
 
+/*
+ * Fixed-point search (Section IV, Precision and Numerical Accuracy: signed
+ * 16-bit words, the number of fractional bits studied from 8 to 13).
+ *   frac_bits  0: the floating-point search (the default);
+ *              1..15: the descent holds the level residuals in units of tau
+ *              (the effective points of Eq. 17) and the normalised factor
+ *              entries U~_mk = U_mk / U_mm as 16-bit words with frac_bits
+ *              fractional bits: each is rounded to the nearest multiple of
+ *              2^-frac_bits (halves to even) and saturated to
+ *              +-32767 2^-frac_bits, every column update saturates the same
+ *              way, and DEMAP ranks the quantised point exactly (ties to the
+ *              smaller alphabet index). The PEDs are summed in FP32; l, gamma
+ *              and x are then computed for the chosen perturbation exactly as
+ *              in the floating-point search.
+ * The 16-bit arithmetic is carried out exactly in FP32 registers (every word
+ * and every sum of two words is representable). Only with VP_DEMAP_EXACT:
+ * frac_bits > 0 with the LUT DEMAP (set in either order) is invalid, as is a
+ * value outside 0..15. Takes effect at the next vp_precode.
+ */
+vp_status vp_plan_set_fixed_point(vp_plan* plan, int frac_bits);
+
 /* Free the plan and its device state. Synchronises the device first so that
  * no enqueued work still reads the state. NULL is accepted. */
 vp_status vp_plan_destroy(vp_plan* plan);

@@ -21,8 +21,9 @@ from . import _build
 
 __all__ = [
     "VPError", "load", "build", "library_path",
-    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap", "vp_plan_destroy",
-    "vp_factorize", "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
+    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
+    "vp_plan_set_fixed_point", "vp_plan_destroy", "vp_factorize", "vp_precode", "vp_get_paths", "vp_run_slot_host",
+    "vp_last_launch_count", "vp_status_string",
     "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_problem_desc", "vp_batch_create", "VP_DEMAP_EXACT", "VP_DEMAP_LUT",
     "vp_batch_workspace_bytes", "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy",
     "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
@@ -40,7 +41,8 @@ VP_DEMAP_EXACT = 0
 VP_DEMAP_LUT = 1
 
 EXPORTED_SYMBOLS = (
-    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap", "vp_plan_destroy",
+    "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
+    "vp_plan_set_fixed_point", "vp_plan_destroy",
     "vp_factorize",
     "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
@@ -90,6 +92,7 @@ def load():
             L.vp_plan_set_fp64_threshold.argtypes = [vpp, ctypes.c_float]
             L.vp_plan_set_lambda.argtypes = [vpp, ctypes.c_float]
             L.vp_plan_set_demap.argtypes = [vpp, ctypes.c_int]
+            L.vp_plan_set_fixed_point.argtypes = [vpp, ctypes.c_int]
             L.vp_plan_destroy.argtypes = [vpp]
             L.vp_factorize.argtypes = [vpp, vpp, ctypes.c_int, vpp, vpp, vpp, vpp, vpp]
             L.vp_precode.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp]
@@ -115,7 +118,7 @@ def load():
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
             for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
-                         "vp_plan_destroy",
+                         "vp_plan_set_fixed_point", "vp_plan_destroy",
                          "vp_factorize",
                          "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_precode_noalloc", "vp_batch_create",
                          "vp_batch_bind", "vp_batch_launch", "vp_batch_destroy", "vp_precode_batch"):
@@ -176,6 +179,10 @@ def vp_plan_set_lambda(plan: int, lam: float) -> None:
 
 def vp_plan_set_demap(plan: int, demap: int) -> None:
     _check(load().vp_plan_set_demap(plan, int(demap)), "vp_plan_set_demap")
+
+
+def vp_plan_set_fixed_point(plan: int, frac_bits: int) -> None:
+    _check(load().vp_plan_set_fixed_point(plan, int(frac_bits)), "vp_plan_set_fixed_point")
 
 
 def vp_plan_destroy(plan: int) -> None:
@@ -326,7 +333,7 @@ class Plan:
     """Owning handle of a vp_plan (destroys it on close / exit of a with-block)."""
 
     def __init__(self, K: int, M: int, qam: int, n_paths: int, tau: float = 0.0,
-                 fp64_threshold: float | None = None, lam: float = 0.0, demap: int = 0):
+                 fp64_threshold: float | None = None, lam: float = 0.0, demap: int = 0, frac_bits: int = 0):
         self.K, self.M, self.qam, self.n_paths = K, M, qam, n_paths
         self.handle = vp_plan_create(K, M, qam, n_paths, tau)
         if fp64_threshold is not None:
@@ -335,6 +342,8 @@ class Plan:
             vp_plan_set_lambda(self.handle, lam)
         if demap:
             vp_plan_set_demap(self.handle, demap)
+        if frac_bits:
+            vp_plan_set_fixed_point(self.handle, frac_bits)
 
     def close(self):
         if self.handle:

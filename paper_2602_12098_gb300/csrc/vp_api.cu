@@ -158,7 +158,16 @@ vp_status vp_plan_set_lambda(vp_plan* p, float lambda)
 vp_status vp_plan_set_demap(vp_plan* p, int demap)
 {
     if (!p || (demap != VP_DEMAP_EXACT && demap != VP_DEMAP_LUT)) return VP_ERR_INVALID_ARG;
+    if (demap == VP_DEMAP_LUT && p->frac_bits > 0) return VP_ERR_INVALID_ARG;
     p->demap = demap;
+    return VP_OK;
+}
+
+vp_status vp_plan_set_fixed_point(vp_plan* p, int frac_bits)
+{
+    if (!p || frac_bits < 0 || frac_bits > 15) return VP_ERR_INVALID_ARG;
+    if (frac_bits > 0 && p->demap != VP_DEMAP_EXACT) return VP_ERR_INVALID_ARG;
+    p->frac_bits = frac_bits;
     return VP_OK;
 }
 

@@ -143,6 +143,7 @@ struct vp_plan {
     float kappa_thr = 1e4f;
     float lambda = 0.f;   // Tikhonov parameter (Hbar = [H lambda*I])
     int demap = VP_DEMAP_EXACT;
+    int frac_bits = 0;                  // fixed-point search with 16-bit words (0 = floating point)
     int cap = 0;   // channel capacity of `d`
     int cap_mp = 0;  // rows of P that `d` was allocated for
     int C = 0;     // channels of the last vp_factorize

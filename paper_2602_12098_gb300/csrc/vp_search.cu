@@ -16,6 +16,16 @@
 // antenna rows of w / sqrt(gamma) (with lambda > 0, P has K more rows: the
 // regularisation part of Alg. 2's w, which counts in gamma but is not sent),
 // the product P u formed with exact products and compensated sums.
+//
+// Fixed-point form (FIX, Section IV's 16-bit datapath with F fractional
+// bits): the entries of U~ are rounded to multiples of 2^-F (halves to even)
+// and saturated to +-32767 2^-F; the starting residual b' = (s + U~ s) / tau
+// is formed from those words and rounded once, and every column update
+// saturates. Words, the sum of two of them, and b' before its rounding
+// (odd integers <= 15 times words: numerators below 2^24 units of 2^-F for
+// K <= 16) are all exact in FP32, so the FMAs perform the integer arithmetic
+// exactly; DEMAP then works on dyadic points with the tie shift scaled to
+// the word (below).
 #include "vp_internal.cuh"
 
 namespace vp {
@@ -40,7 +50,31 @@ struct SearchArgs {
     const int* ids;
     int KM, NP;
     int demap;       // VP_DEMAP_* (plan launches)
+    int frac;        // fractional bits of the fixed-point search (0: floating point)
 };
+
+// Fixed-point parameters of a launch: the word scale 2^F and its inverse, the
+// saturation bound 32767 2^-F and the DEMAP tie shift.
+struct FixP {
+    float scale, inv_scale, lim, epsx, epsy;
+};
+
+__device__ __forceinline__ FixP fix_params(int F)
+{
+    FixP f;
+    f.scale = __int_as_float((127 + F) << 23);
+    f.inv_scale = __int_as_float((127 - F) << 23);
+    f.lim = 32767.f * f.inv_scale;
+    f.epsx = __int_as_float((127 - F - 2) << 23);    // 2^-(F+2)
+    f.epsy = __int_as_float((127 - F - 4) << 23);    // 2^-(F+4)
+    return f;
+}
+
+// a real value as a word: round half to even, saturate
+__device__ __forceinline__ float qword(float v, const FixP& f)
+{
+    return fminf(fmaxf(rintf(v * f.scale), -32767.f), 32767.f) * f.inv_scale;
+}
 
 // DEMAP selection: the q-th (0-based) nearest point t of {-1,0,1}+j{-1,0,1}
 // to the effective point c = (x, y), ties to the smaller alphabet index
@@ -62,6 +96,13 @@ struct SearchArgs {
 // and every pair not ordered by the table's structure is one of
 //   f0 A<B, f1 C<B, f2 A<D, f3 C<D, f4 E<C, f5 E<D, f6 F<C, f7 G<D, f8 F<G,
 // so the rank of each cell is a short sum of these bits.
+//
+// In the fixed-point search every centre is a multiple of 2^-F and may reach
+// 32767 2^-F, where 2^-23 is below the spacing of floats; there the shift is
+// (2^-(F+2), 2^-(F+4)): distinct squared distances of such centres differ by
+// at least 2^(1-F), the shift moves a difference by at most 1.25 2^-F, and it
+// still orders ties by (tr, ti) since eps_x > 2 eps_y. The shifted centre and
+// every gap below keep <= 21 significant bits, so all of it is exact in FP32.
 constexpr float kEpsX = 0x1p-23f;
 constexpr float kEpsY = 0x1p-25f;
 __device__ __forceinline__ float gap1(float x) { return fabsf(fmaf(-2.f, fabsf(x), 1.f)); }
@@ -91,9 +132,10 @@ __device__ __forceinline__ void rank_cell(float D1x, float D2x, float D1y, float
 // branches only choose the cell (ci, cj). Per axis the points in increasing
 // distance are n0 (the clamped rounding), s - n0 and -s, s = +1 for x > 0
 // else -1 (the three points of {-1, 0, 1} sum to zero).
-__device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, int& tr, int& ti)
+__device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, int& tr, int& ti,
+                                             float epsx = kEpsX, float epsy = kEpsY)
 {
-    const float px = cx - kEpsX, py = cy - kEpsY;
+    const float px = cx - epsx, py = cy - epsy;
     const int n0x = (px > 0.5f) - (px <= -0.5f);
     const int n0y = (py > 0.5f) - (py <= -0.5f);
     if (mq == 0) {
@@ -170,10 +212,10 @@ __device__ void build_lut(uint64_t* lut)
     }
 }
 
-template <int KT, bool LUT>
+template <int KT, bool LUT, bool FIX>
 __device__ __forceinline__ void level_step(int lv, const float4* utp, const float* wv, uint32_t cw0, uint32_t cw1,
-                                           uint32_t mq0, uint32_t mq1, const uint64_t* lut, float2 (&r)[KT],
-                                           float& ped, uint32_t& lc0, uint32_t& lc1)
+                                           uint32_t mq0, uint32_t mq1, const uint64_t* lut, const FixP& fx,
+                                           float2 (&r)[KT], float& ped, uint32_t& lc0, uint32_t& lc1)
 {
     const int sh = 4 * (lv & 7);
     const int q = (int)(((lv < 8) ? cw0 : cw1) >> sh) & 15;
@@ -183,7 +225,8 @@ __device__ __forceinline__ void level_step(int lv, const float4* utp, const floa
         select_lut(cx, cy, q, lut, tr, ti);
     } else {
         const int mql = (int)(((lv < 8) ? mq0 : mq1) >> sh) & 15;
-        select_point(cx, cy, q, mql, tr, ti);
+        if (FIX) select_point(cx, cy, q, mql, tr, ti, fx.epsx, fx.epsy);
+        else select_point(cx, cy, q, mql, tr, ti);
     }
     const float ftr = (float)tr, fti = (float)ti;
     const float dx = cx - ftr, dy = cy - fti;
@@ -199,6 +242,10 @@ __device__ __forceinline__ void level_step(int lv, const float4* utp, const floa
                 const float4 u = utp[m * KT + lv];
                 r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
                 r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
+                if (FIX) {
+                    r[m].x = fminf(fmaxf(r[m].x, -fx.lim), fx.lim);
+                    r[m].y = fminf(fmaxf(r[m].y, -fx.lim), fx.lim);
+                }
             }
         }
     }
@@ -248,7 +295,7 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
 // then continues from its prefix's state through the remaining levels. The
 // arithmetic per path is the same as a full descent, so results are
 // identical; the shared levels are the ones with the most column updates.
-template <int KT, bool BATCH, bool LUT>
+template <int KT, bool BATCH, bool LUT, bool FIX>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -314,11 +361,18 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         return;
     }
 
+    const FixP fx = fix_params(FIX ? a.frac : 0);
     for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
         const int r = i / KT, q = i % KT;
         const bool in = r < K && q < K;
-        utp[i] = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        utc[i] = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
+        float4 u = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 uc = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
+        if (FIX) {
+            u = make_float4(qword(u.x, fx), qword(u.y, fx), qword(u.z, fx), qword(u.w, fx));
+            uc = make_float2(qword(uc.x, fx), qword(uc.y, fx));
+        }
+        utp[i] = u;
+        utc[i] = uc;
     }
     for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
         pt[i] = cs.pt[i];
@@ -359,6 +413,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         }
         // residuals are kept in units of tau: r' = r / tau is the effective point of Eq. (17)
         b = make_float2(b.x * inv_tau, b.y * inv_tau);
+        if (FIX) b = make_float2(qword(b.x, fx), qword(b.y, fx));
         if (lane < KT) bw[lane] = (lane < K) ? b : make_float2(0.f, 0.f);
         float g0 = (lane < K) ? wv[lane] * cabs2(b) : 0.f;     // zero candidate: ||U s||^2
 #pragma unroll
@@ -378,8 +433,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
             for (int lv = KT - 1; lv >= kLo; --lv) {
                 if (lv >= KT - T)
-                    level_step<KT, LUT>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, r, ped,
-                                        lc0, lc1);
+                    level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, fx,
+                                             r, ped, lc0, lc1);
             }
             if (lane < NPF) {
 #pragma unroll
@@ -412,8 +467,8 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
             for (int lv = KT - 1; lv >= 0; --lv) {
                 if (lv < KB)
-                    level_step<KT, LUT>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, r, ped,
-                                        lc0, lc1);
+                    level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, fx,
+                                             r, ped, lc0, lc1);
             }
             if (vld && (ped < bp || (ped == bp && rk < brk))) { bp = ped; brk = rk; blc0 = lc0; blc1 = lc1; }
         }
@@ -469,17 +524,17 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     }
 }
 
-template <int KT, bool BATCH, bool LUT>
+template <int KT, bool BATCH, bool LUT, bool FIX>
 cudaError_t launch_one(const SearchArgs& a, int C, int threads, size_t sh, cudaStream_t s)
 {
     static size_t attr = 0;
     if (sh > 40 * 1024 && sh > attr) {
-        cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, BATCH, LUT>,
+        cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, BATCH, LUT, FIX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
         if (e != cudaSuccess) return e;
         attr = sh;
     }
-    search_kernel<KT, BATCH, LUT><<<C, threads, sh, s>>>(a);
+    search_kernel<KT, BATCH, LUT, FIX><<<C, threads, sh, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -489,9 +544,10 @@ cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
     const int NW = threads / 32;
     const int KM = a.probs ? a.KM : a.K * a.Mp, NP = a.probs ? a.NP : a.n;
     const size_t sh = (size_t)search_smem(KT, KM, NP, NW).total;
-    if (a.probs) return launch_one<KT, true, false>(a, C, threads, sh, s);
-    if (a.demap == VP_DEMAP_LUT) return launch_one<KT, false, true>(a, C, threads, sh, s);
-    return launch_one<KT, false, false>(a, C, threads, sh, s);
+    if (a.probs) return launch_one<KT, true, false, false>(a, C, threads, sh, s);
+    if (a.frac > 0) return launch_one<KT, false, false, true>(a, C, threads, sh, s);
+    if (a.demap == VP_DEMAP_LUT) return launch_one<KT, false, true, false>(a, C, threads, sh, s);
+    return launch_one<KT, false, false, false>(a, C, threads, sh, s);
 }
 
 }  // namespace
@@ -512,6 +568,7 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     a.M = p->M;
     a.Mp = p_rows(p);
     a.demap = p->demap;
+    a.frac = p->frac_bits;
     a.n = p->n_paths;
     a.nch = n_chunks(p->n_paths);
     int m = 1;

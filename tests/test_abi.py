@@ -133,3 +133,24 @@ def test_demap_option_validation():
             assert e.value.code == 1
     finally:
         vp.vp_plan_destroy(h)
+
+
+def test_fixed_point_option_validation():
+    h = vp.vp_plan_create(4, 4, 16, 16)
+    try:
+        for f in (1, 8, 13, 15, 0):
+            vp.vp_plan_set_fixed_point(h, f)
+        for bad in (-1, 16, 40):
+            with pytest.raises(vp.VPError) as e:
+                vp.vp_plan_set_fixed_point(h, bad)
+            assert e.value.code == 1
+        # only with the exact DEMAP, whichever is set first
+        vp.vp_plan_set_fixed_point(h, 11)
+        with pytest.raises(vp.VPError):
+            vp.vp_plan_set_demap(h, vp.VP_DEMAP_LUT)
+        vp.vp_plan_set_fixed_point(h, 0)
+        vp.vp_plan_set_demap(h, vp.VP_DEMAP_LUT)
+        with pytest.raises(vp.VPError):
+            vp.vp_plan_set_fixed_point(h, 11)
+    finally:
+        vp.vp_plan_destroy(h)
