@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
     ap.add_argument("--serving-slots", type=int, default=2000)
-    ap.add_argument("--serving-streams", type=int, default=8)
+    ap.add_argument("--serving-lanes", type=int, default=8)
+    ap.add_argument("--serving-pool-mib", type=int, default=256)
     return ap.parse_args()
 
 
@@ -425,20 +426,22 @@ def measure_fixed(dev, b, w, flush, steps: int, fracs=(8, 9, 10, 11, 12, 13)) ->
     return out
 
 
-def measure_serving(dev, n_slots: int, nstreams: int = 8) -> dict:
-    """Open-loop serving: Poisson job arrivals (mean 4 per 0.5 ms slot); a job
-    is one cell's slot, 3276 subcarriers x 14 symbols, K in {4, 8, 12, 16},
-    M = 16, Q in {16, 64, 256}, n = 64, iid channels. Jobs are dispatched at
-    their arrival times round-robin over `nstreams` streams (a plan per job type and
-    stream); latency = GPU completion - arrival, on one clock through a
-    reference event. Inputs are one draw per job type, reused by its jobs."""
+def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 256) -> dict:
+    """Open-loop serving through the job server (vp_server_*): Poisson job
+    arrivals (mean 4 per 0.5 ms slot); a job is one cell's slot, 3276
+    subcarriers x 14 symbols, K in {4, 8, 12, 16}, M = 16, Q in {16, 64, 256},
+    n = 64, iid channels. Each job is submitted at its arrival time; the
+    server admits it when one of `lanes` streams is idle and its state fits
+    in the `pool_mib` pool, oldest first. Latency = the job's device end time
+    - its arrival, both from the server's clock zero. Inputs are one draw per
+    job type, reused by its jobs (timing only: outputs rotate over `lanes`
+    buffers per type)."""
     import numpy as np
     import torch
 
     import paper_2602_12098_gb300 as vp
     from paper_2602_12098_gb300 import workloads as W
     jobs = W.poisson_jobs(n_slots)
-    streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
     types = sorted({(j.K, j.M, j.qam, j.n_paths) for j in jobs})
     bufs = {}
     for t in types:
@@ -446,61 +449,58 @@ def measure_serving(dev, n_slots: int, nstreams: int = 8) -> dict:
         proto = next(j for j in jobs if (j.K, j.M, j.qam, j.n_paths) == t)
         Hn, sn = W.job_inputs(proto)
         C, V = Hn.shape[0], sn.shape[0]
-        bufs[t] = {"H": torch.from_numpy(Hn).to(dev), "sym": torch.from_numpy(sn).to(dev), "C": C, "V": V,
-                   "S": proto.symbols,
-                   "out": [(torch.empty((V, M), dtype=torch.complex64, device=dev),
-                            torch.empty((V, K, 2), dtype=torch.int8, device=dev),
-                            torch.empty((V,), dtype=torch.float32, device=dev)) for _ in range(nstreams)],
-                   "plans": [vp.Plan(K, M, qam, n) for _ in range(nstreams)]}
-    lib = vp.load()
-
-    def enqueue(t, k):
-        bb = bufs[t]
-        h = bb["plans"][k].handle
-        x, l, g = bb["out"][k]
-        sh = streams[k].cuda_stream
-        if lib.vp_factorize(h, bb["H"].data_ptr(), bb["C"], None, None, None, None, sh) != 0:
-            raise RuntimeError("vp_factorize failed")
-        if lib.vp_precode(h, bb["sym"].data_ptr(), bb["S"], None, bb["V"], x.data_ptr(), l.data_ptr(),
-                          g.data_ptr(), sh) != 0:
-            raise RuntimeError("vp_precode failed")
-
+        H, sym = torch.from_numpy(Hn).to(dev), torch.from_numpy(sn).to(dev)
+        outs = [(torch.empty((V, M), dtype=torch.complex64, device=dev),
+                 torch.empty((V, K, 2), dtype=torch.int8, device=dev),
+                 torch.empty((V,), dtype=torch.float32, device=dev)) for _ in range(lanes)]
+        bufs[t] = {"V": V, "descs": [vp.job_desc(K, M, qam, n, C, proto.symbols, H, sym, x, l, g)
+                                     for x, l, g in outs], "used": 0}
     torch.cuda.synchronize()
-    for t in types:                      # allocate plan state and warm up
-        for k in range(nstreams):
-            enqueue(t, k)
-    torch.cuda.synchronize()
-    ends = [torch.cuda.Event(enable_timing=True) for _ in jobs]
-    ref = torch.cuda.Event(enable_timing=True)
-    ref.record(streams[0])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    late_dispatch = 0.0
-    for i, j in enumerate(jobs):
-        target = t0 + j.arrival_us * 1e-6
-        while True:
-            now = time.perf_counter()
-            if now >= target:
-                break
-        late_dispatch = max(late_dispatch, now - target)
-        k = i % nstreams
-        t = (j.K, j.M, j.qam, j.n_paths)
-        enqueue(t, k)
-        ends[i].record(streams[k])
-    torch.cuda.synchronize()
-    lat = np.array([ref.elapsed_time(e) - j.arrival_us * 1e-3 for e, j in zip(ends, jobs)])   # ms
-    done = max(ref.elapsed_time(e) for e in ends)
-    vecs = sum(bufs[(j.K, j.M, j.qam, j.n_paths)]["V"] for j in jobs)
-    for t in types:
-        for p in bufs[t]["plans"]:
-            p.close()
+    with vp.Server(pool_mib << 20, lanes) as srv:
+        for t in types:                      # warm-up: every job type once
+            for d in bufs[t]["descs"]:
+                srv.submit(d)
+        srv.drain(60.0)
+        srv.poll()
+        arrive = {}
+        done = {}
+        srv.reset_clock()
+        t0 = time.perf_counter()
+        late = 0.0
+        for j in jobs:
+            target = t0 + j.arrival_us * 1e-6
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                for rec in srv.poll():
+                    done[rec[0]] = rec
+            late = max(late, now - target)
+            bb = bufs[(j.K, j.M, j.qam, j.n_paths)]
+            jid = srv.submit(bb["descs"][bb["used"] % lanes])
+            bb["used"] += 1
+            arrive[jid] = (j.arrival_us * 1e-3, bb["V"])
+        srv.drain(600.0)
+        for rec in srv.poll():
+            done[rec[0]] = rec
+        st = srv.stats()
+    if sorted(done) != sorted(arrive) or any(rec[1] != 0 for rec in done.values()):
+        raise RuntimeError("serving: a job failed or was not reported")
+    lat = np.array([done[i][3] - arrive[i][0] for i in arrive])
+    wait = np.array([done[i][2] - arrive[i][0] for i in arrive])
+    end = max(rec[3] for rec in done.values())
+    vecs = sum(v for _, v in arrive.values())
     return {"workload": f"Poisson arrivals, mean 4 jobs per 0.5 ms slot, {n_slots} slots; job = 3276 subcarriers "
                         "x 14 symbols, K in {4,8,12,16}, M 16, Q in {16,64,256}, n 64, iid",
+            "engine": f"vp_server: {lanes} lanes (streams), {pool_mib} MiB state pool, first come first served "
+                      "admission by idle lane and pool space",
             "jobs": len(jobs), "p50_job_ms": float(np.percentile(lat, 50)), "p99_job_ms": float(np.percentile(lat, 99)),
+            "p50_admission_wait_ms": float(np.percentile(wait, 50)),
             "deadline_ms": 0.5, "deadline_miss_frac": float(np.mean(lat > 0.5)),
-            "vectors_per_s": vecs / (done / 1e3),
-            "offered_vectors_per_s": vecs / (jobs[-1].arrival_us * 1e-6), "streams": nstreams,
-            "max_dispatch_lag_ms": 1e3 * late_dispatch}
+            "vectors_per_s": vecs / (end / 1e3),
+            "offered_vectors_per_s": vecs / (jobs[-1].arrival_us * 1e-6),
+            "max_in_flight": st["max_in_flight"], "pool_high_water_mib": st["pool_high_water"] / 2**20,
+            "max_dispatch_lag_ms": 1e3 * late}
 
 
 def run_gpu(args):
@@ -644,7 +644,7 @@ def run_gpu(args):
         line["fixed_point"] = measure_fixed(dev, b, w, flush, min(args.steps, 20))
         line["batched"] = measure_batched(dev, flush)
     if ws == 1 and not args.no_serving:
-        line["serving"] = measure_serving(dev, args.serving_slots, args.serving_streams)
+        line["serving"] = measure_serving(dev, args.serving_slots, args.serving_lanes, args.serving_pool_mib)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

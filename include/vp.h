@@ -312,6 +312,116 @@ vp_status vp_precode_batch(const vp_problem_desc* descs, int n_problems, size_t 
 /* Workspace of vp_precode_batch for these descriptors (0 if any is invalid). */
 size_t vp_precode_batch_workspace_bytes(const vp_problem_desc* descs, int n_problems);
 
+/*
+ * Serving: a job server that runs whole slots (jobs) as they arrive, on
+ * several CUDA streams ("lanes") at once, with admission by device memory.
+ * The paper's accelerator streams one cell's slot through its pipeline; a
+ * GPU serving many cells instead admits each arriving job as soon as a lane
+ * and the job's per-channel state fit, so that jobs that arrive while others
+ * run overlap with them on the device. Each job is one slot of one plan
+ * shape: vp_factorize + vp_precode over C channels and S symbols per channel
+ * (the same kernels, so a job's outputs do not depend on what runs beside it).
+ *
+ * Memory. vp_server_create reserves one device pool (one cudaMalloc); a job
+ * holds a piece of it, its per-channel state (about 24 K^2 + 16 K Mp +
+ * 20 n_paths + 5 K + 300 bytes per channel, Mp = M or M + K with lambda > 0), from
+ * admission until the server sees it finished. Inputs and outputs stay
+ * caller-owned device memory.
+ *
+ * Admission is first come, first served: the oldest waiting job is admitted
+ * when a lane is idle and its state fits in the pool (first fit); a job that
+ * does not fit waits, and the jobs behind it wait too. A job that could never
+ * fit (larger than the whole pool) is refused at submission.
+ *
+ * Progress happens inside vp_server_submit, vp_server_poll and
+ * vp_server_drain (no background thread): each retires the jobs whose last
+ * kernel has finished (frees their state and lane) and admits waiting jobs.
+ * The calls may come from different host threads (they take the server's
+ * lock).
+ *
+ * Time. Job times are device times in milliseconds since the last
+ * vp_server_reset_clock (one event on lane 0, waited for by the host before
+ * that call returns), from the events recorded on the job's lane before its
+ * first and after its last kernel.
+ */
+typedef struct vp_server vp_server;
+
+typedef struct {
+    int K, M, qam, n_paths;  /* as vp_plan_create */
+    float tau;               /* 0 = 2 sqrt(qam) */
+    float lambda;            /* as vp_plan_set_lambda (0 = plain sorted RQ) */
+    float fp64_threshold;    /* as vp_plan_set_fp64_threshold; 0 = the default 1e4 */
+    int demap;               /* vp_demap */
+    int frac_bits;           /* as vp_plan_set_fixed_point */
+    int C, S;                /* channels (>= 1), data vectors per channel (>= 0) */
+    const void* H;           /* complex64 [C][K][M] */
+    const uint8_t* sym_idx;  /* uint8 [C*S][K] (vector v -> channel v / S) */
+    void* x;                 /* complex64 [C*S][M] */
+    int8_t* l;               /* int8 [C*S][K][2] */
+    float* gamma;            /* float [C*S] */
+    uint8_t* status;         /* optional uint8 [C] */
+    void* ready_event;       /* optional cudaEvent_t the job's lane waits for
+                                before reading H and sym_idx (NULL: the inputs
+                                are ready when vp_server_submit is called) */
+} vp_job_desc;
+
+typedef struct {
+    int64_t id;        /* as returned by vp_server_submit */
+    int status;        /* VP_OK, or VP_ERR_CUDA if a launch failed */
+    float admit_ms;    /* device time of admission (its first kernel enqueued after) */
+    float end_ms;      /* device time when its last kernel finished */
+} vp_job_done;
+
+typedef struct {
+    int lanes, queued, in_flight, max_in_flight;
+    int64_t submitted, completed;
+    size_t pool_bytes, pool_used, pool_high_water;
+} vp_server_stats;
+
+/*
+ * Create a server on the current device.
+ *   pool_bytes  device memory for the admitted jobs' state (>= 1 MiB)
+ *   lanes       CUDA streams, 1..32; at most that many jobs run at once
+ * Returns VP_ERR_INVALID_ARG for out-of-range arguments, VP_ERR_OOM if the
+ * pool cannot be allocated.
+ */
+vp_status vp_server_create(size_t pool_bytes, int lanes, vp_server** out);
+
+/*
+ * Queue a job (the descriptor is copied; the device buffers it points to
+ * must stay valid until the job is reported done) and admit what fits.
+ * Writes the job's id (1, 2, ...). VP_ERR_INVALID_ARG: a field out of range
+ * (the limits of vp_plan_create and the plan setters); VP_ERR_CAPACITY: the
+ * job's state is larger than the whole pool. Nothing is queued then.
+ */
+vp_status vp_server_submit(vp_server* srv, const vp_job_desc* job, int64_t* id);
+
+/*
+ * Retire finished jobs and admit waiting ones; never blocks on the GPU.
+ * Writes up to `max_done` finished jobs (oldest first) to the HOST array
+ * `done` and their number to *n_done; jobs not written are reported by the
+ * next call.
+ */
+vp_status vp_server_poll(vp_server* srv, vp_job_done* done, int max_done, int* n_done);
+
+/*
+ * Wait until every submitted job has finished (admitting waiting jobs as
+ * lanes and memory free up), or until `timeout_s` seconds have passed
+ * (VP_ERR_TIMEOUT; the jobs keep running). Finished jobs are still reported
+ * by vp_server_poll.
+ */
+vp_status vp_server_drain(vp_server* srv, double timeout_s);
+
+/* Set the zero of the job times (see Time above). */
+vp_status vp_server_reset_clock(vp_server* srv);
+
+/* Counters of the server (HOST struct). */
+vp_status vp_server_get_stats(vp_server* srv, vp_server_stats* out);
+
+/* Wait for every lane, then free the pool, streams and events. NULL is
+ * accepted. Jobs still waiting for admission are dropped. */
+vp_status vp_server_destroy(vp_server* srv);
+
 /* Number of kernel launches the last vp_factorize / vp_precode /
  * vp_run_slot_host call enqueued (copies and memsets not counted). */
 int vp_last_launch_count(const vp_plan* plan);

@@ -27,6 +27,8 @@ __all__ = [
     "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_problem_desc", "vp_batch_create", "VP_DEMAP_EXACT", "VP_DEMAP_LUT",
     "vp_batch_workspace_bytes", "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy",
     "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
+    "vp_job_desc", "vp_job_done", "vp_server_stats", "vp_server_create", "vp_server_submit", "vp_server_poll",
+    "vp_server_drain", "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "Server",
     "EXPORTED_SYMBOLS", "Plan",
 ]
 
@@ -48,7 +50,8 @@ EXPORTED_SYMBOLS = (
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
     "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_batch_create", "vp_batch_workspace_bytes",
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
-    "vp_precode_batch_workspace_bytes",
+    "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
+    "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy",
 )
 
 
@@ -58,6 +61,27 @@ class vp_problem_desc(ctypes.Structure):
                 ("tau", ctypes.c_float), ("S", ctypes.c_int), ("H", ctypes.c_void_p), ("sym_idx", ctypes.c_void_p),
                 ("x", ctypes.c_void_p), ("l", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
                 ("status", ctypes.c_void_p)]
+
+
+class vp_job_desc(ctypes.Structure):
+    """One job of the server: a slot of one plan shape (layout of the C struct)."""
+    _fields_ = [("K", ctypes.c_int), ("M", ctypes.c_int), ("qam", ctypes.c_int), ("n_paths", ctypes.c_int),
+                ("tau", ctypes.c_float), ("lam", ctypes.c_float), ("fp64_threshold", ctypes.c_float),
+                ("demap", ctypes.c_int), ("frac_bits", ctypes.c_int), ("C", ctypes.c_int), ("S", ctypes.c_int),
+                ("H", ctypes.c_void_p), ("sym_idx", ctypes.c_void_p), ("x", ctypes.c_void_p), ("l", ctypes.c_void_p),
+                ("gamma", ctypes.c_void_p), ("status", ctypes.c_void_p), ("ready_event", ctypes.c_void_p)]
+
+
+class vp_job_done(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("admit_ms", ctypes.c_float),
+                ("end_ms", ctypes.c_float)]
+
+
+class vp_server_stats(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int), ("queued", ctypes.c_int), ("in_flight", ctypes.c_int),
+                ("max_in_flight", ctypes.c_int), ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("pool_bytes", ctypes.c_size_t), ("pool_used", ctypes.c_size_t), ("pool_high_water", ctypes.c_size_t)]
+
 
 _lock = threading.Lock()
 _lib = None
@@ -115,6 +139,17 @@ def load():
             L.vp_precode_batch.argtypes = [descp, ctypes.c_int, ctypes.c_size_t, vpp, vpp]
             L.vp_precode_batch_workspace_bytes.argtypes = [descp, ctypes.c_int]
             L.vp_precode_batch_workspace_bytes.restype = ctypes.c_size_t
+            sp = ctypes.c_void_p
+            L.vp_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(sp)]
+            L.vp_server_submit.argtypes = [sp, ctypes.POINTER(vp_job_desc), ctypes.POINTER(ctypes.c_int64)]
+            L.vp_server_poll.argtypes = [sp, ctypes.POINTER(vp_job_done), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+            L.vp_server_drain.argtypes = [sp, ctypes.c_double]
+            L.vp_server_reset_clock.argtypes = [sp]
+            L.vp_server_get_stats.argtypes = [sp, ctypes.POINTER(vp_server_stats)]
+            L.vp_server_destroy.argtypes = [sp]
+            for name in ("vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
+                         "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy"):
+                getattr(L, name).restype = ctypes.c_int
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
             for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
@@ -314,6 +349,96 @@ class Batch:
     def close(self):
         if self.handle:
             vp_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vp_server_create(pool_bytes: int, lanes: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().vp_server_create(int(pool_bytes), int(lanes), ctypes.byref(h)), "vp_server_create")
+    return h.value
+
+
+def vp_server_submit(server: int, job: vp_job_desc) -> int:
+    i = ctypes.c_int64()
+    _check(load().vp_server_submit(server, ctypes.byref(job), ctypes.byref(i)), "vp_server_submit")
+    return i.value
+
+
+def vp_server_poll(server: int, max_done: int = 256) -> list:
+    """Finished jobs since the last poll: list of (id, status, admit_ms, end_ms)."""
+    buf = (vp_job_done * max(int(max_done), 1))()
+    n = ctypes.c_int()
+    out = []
+    while True:
+        _check(load().vp_server_poll(server, buf, len(buf), ctypes.byref(n)), "vp_server_poll")
+        out += [(buf[i].id, buf[i].status, buf[i].admit_ms, buf[i].end_ms) for i in range(n.value)]
+        if n.value < len(buf):
+            return out
+
+
+def vp_server_drain(server: int, timeout_s: float = 60.0) -> None:
+    _check(load().vp_server_drain(server, float(timeout_s)), "vp_server_drain")
+
+
+def vp_server_reset_clock(server: int) -> None:
+    _check(load().vp_server_reset_clock(server), "vp_server_reset_clock")
+
+
+def vp_server_get_stats(server: int) -> dict:
+    st = vp_server_stats()
+    _check(load().vp_server_get_stats(server, ctypes.byref(st)), "vp_server_get_stats")
+    return {k: getattr(st, k) for k, _ in vp_server_stats._fields_}
+
+
+def vp_server_destroy(server: int) -> None:
+    _check(load().vp_server_destroy(server), "vp_server_destroy")
+
+
+def job_desc(K, M, qam, n_paths, C, S, H, sym, x, l, gamma, status=None, tau=0.0, lam=0.0, fp64_threshold=0.0,
+             demap=0, frac_bits=0, ready_event=None) -> vp_job_desc:
+    """A vp_job_desc from torch device tensors (or raw addresses)."""
+    return vp_job_desc(int(K), int(M), int(qam), int(n_paths), float(tau), float(lam), float(fp64_threshold),
+                       int(demap), int(frac_bits), int(C), int(S), _addr(H), _addr(sym), _addr(x), _addr(l),
+                       _addr(gamma), _addr(status),
+                       _addr(getattr(ready_event, "cuda_event", ready_event)))
+
+
+class Server:
+    """Owning handle of a vp_server (destroys it on close / exit of a with-block)."""
+
+    def __init__(self, pool_bytes: int, lanes: int = 4):
+        self.handle = vp_server_create(pool_bytes, lanes)
+
+    def submit(self, job: vp_job_desc) -> int:
+        return vp_server_submit(self.handle, job)
+
+    def poll(self) -> list:
+        return vp_server_poll(self.handle)
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        vp_server_drain(self.handle, timeout_s)
+
+    def reset_clock(self) -> None:
+        vp_server_reset_clock(self.handle)
+
+    def stats(self) -> dict:
+        return vp_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            vp_server_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

@@ -181,6 +181,15 @@ inline int qam_side(int qam)
     return m;
 }
 
+// Per-channel state of C channels laid out from `base` in 256-byte aligned
+// pieces; returns the bytes used (base = null only measures).
+size_t carve_state(unsigned char* base, int C, int K, int Mp, int n, DeviceState* d);
+
+// One slot on p's state (vp_factorize + vp_precode without the optional
+// outputs): memset, factor32, factor64, pathsel, status copy, search.
+cudaError_t enqueue_slot(const vp_plan* p, const float2* H, int C, const uint8_t* sym, int S, float2* x, int8_t* l,
+                         float* gamma, uint8_t* status, cudaStream_t s);
+
 // Kernel launchers (each returns cudaSuccess or the launch error).
 cudaError_t launch_factor32(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
                             uint8_t* ul_out, cudaStream_t s);

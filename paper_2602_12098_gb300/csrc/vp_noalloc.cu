@@ -44,8 +44,13 @@ vp_status scratch_address(void** out)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Lays the state of C channels out in the array; returns the bytes used.
-size_t carve(unsigned char* base, int C, int K, int Mp, int n, vp::DeviceState* d)
+}  // namespace
+
+namespace vp {
+
+// Lays the state of C channels out from `base` (256-byte aligned pieces);
+// returns the bytes used. base = null only measures.
+size_t carve_state(unsigned char* base, int C, int K, int Mp, int n, DeviceState* d)
 {
     const size_t nch = (size_t)vp::n_chunks(n);
     size_t off = 0;
@@ -72,7 +77,24 @@ size_t carve(unsigned char* base, int C, int K, int Mp, int n, vp::DeviceState* 
     return off;
 }
 
-}  // namespace
+// One slot on the plan's state: factorise C channels, select paths, copy the
+// status bytes, and precode S vectors per channel. Returns the first failing
+// launch's error.
+cudaError_t enqueue_slot(const vp_plan* p, const float2* H, int C, const uint8_t* sym, int S, float2* x, int8_t* l,
+                         float* gamma, uint8_t* status, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->d.nflag, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = launch_factor32(p, H, C, nullptr, nullptr, nullptr, s)) != cudaSuccess) return e;
+    if ((e = launch_factor64(p, H, C, nullptr, nullptr, nullptr, s)) != cudaSuccess) return e;
+    if ((e = launch_pathsel(p, C, s)) != cudaSuccess) return e;
+    if (status && (e = cudaMemcpyAsync(status, p->d.st, (size_t)C, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    if (S > 0 && (e = launch_search(p, sym, S, nullptr, C * S, x, l, gamma, s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+}  // namespace vp
 
 extern "C" {
 
@@ -85,24 +107,17 @@ vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const ui
     if (plan->K > plan->M && !(plan->lambda > 0.f)) return VP_ERR_INVALID_ARG;
     const int mp = vp::p_rows(plan);
     vp::DeviceState probe;
-    if (carve(nullptr, C, plan->K, mp, plan->n_paths, &probe) > kNoAllocBytes) return VP_ERR_CAPACITY;
+    if (vp::carve_state(nullptr, C, plan->K, mp, plan->n_paths, &probe) > kNoAllocBytes) return VP_ERR_CAPACITY;
     void* base = nullptr;
     vp_status st = scratch_address(&base);
     if (st != VP_OK) return st;
 
     vp_plan p = *plan;                    // parameters only; the state points into the array
-    carve(static_cast<unsigned char*>(base), C, p.K, mp, p.n_paths, &p.d);
+    vp::carve_state(static_cast<unsigned char*>(base), C, p.K, mp, p.n_paths, &p.d);
     p.cap = C;
     p.C = C;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const float2* h = static_cast<const float2*>(H);
-    if (cudaMemsetAsync(p.d.nflag, 0, sizeof(int), s) != cudaSuccess) return VP_ERR_CUDA;
-    if (vp::launch_factor32(&p, h, C, nullptr, nullptr, nullptr, s) != cudaSuccess) return VP_ERR_CUDA;
-    if (vp::launch_factor64(&p, h, C, nullptr, nullptr, nullptr, s) != cudaSuccess) return VP_ERR_CUDA;
-    if (vp::launch_pathsel(&p, C, s) != cudaSuccess) return VP_ERR_CUDA;
-    if (status && cudaMemcpyAsync(status, p.d.st, (size_t)C, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return VP_ERR_CUDA;
-    if (S > 0 && vp::launch_search(&p, sym_idx, S, nullptr, C * S, static_cast<float2*>(x), l, gamma, s) != cudaSuccess)
+    if (vp::enqueue_slot(&p, static_cast<const float2*>(H), C, sym_idx, S, static_cast<float2*>(x), l, gamma, status,
+                         static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return VP_ERR_CUDA;
     return VP_OK;
 }

@@ -154,3 +154,22 @@ def test_fixed_point_option_validation():
             vp.vp_plan_set_fixed_point(h, 11)
     finally:
         vp.vp_plan_destroy(h)
+
+
+def test_server_argument_validation():
+    """Argument errors of the job server come back before any CUDA call."""
+    for pool, lanes in ((1 << 19, 4), (1 << 20, 0), (1 << 20, 33), (1 << 30, -1)):
+        with pytest.raises(vp.VPError) as e:
+            vp.vp_server_create(pool, lanes)
+        assert e.value.code == 1
+    lib = vp.load()
+    job = vp.job_desc(4, 4, 16, 16, 8, 14, 1, 1, 1, 1, 1)
+    import ctypes
+    i = ctypes.c_int64()
+    n = ctypes.c_int()
+    assert lib.vp_server_submit(None, ctypes.byref(job), ctypes.byref(i)) == 1
+    assert lib.vp_server_poll(None, None, 0, ctypes.byref(n)) == 1
+    assert lib.vp_server_drain(None, 1.0) == 1
+    assert lib.vp_server_reset_clock(None) == 1
+    assert lib.vp_server_get_stats(None, None) == 1
+    assert lib.vp_server_destroy(None) == 0
