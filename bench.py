@@ -47,7 +47,8 @@ def parse():
                     help="run a reduced slot (profiling captures); the default is the full slot")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
-    ap.add_argument("--serving-slots", type=int, default=2000)
+    ap.add_argument("--serving-slots", type=int, default=10000)
+    ap.add_argument("--serving-paths", type=int, default=64)
     ap.add_argument("--serving-lanes", type=int, default=8)
     ap.add_argument("--serving-pool-mib", type=int, default=256)
     return ap.parse_args()
@@ -59,6 +60,33 @@ def paper_work_flops(K: int, M: int, n: int) -> float:
     (Section III-B, with N_t -> K for the tree size), 8 flops (4 FMA) each."""
     cmul = K * M + K * K + n * K * (1 + (K + 1) / 2)
     return 8.0 * cmul
+
+
+def executed_cmul(codes, K: int, M: int, n: int) -> float:
+    """Complex multiplications per vector in the paper's unit (level l of K,
+    1-based from the bottom, costs 1 + l), counting the top T shared levels
+    once per distinct prefix as the search runs them. T per channel is path
+    selection's rule: the largest T <= 3 whose distinct top-T-level prefixes
+    number <= 32, when K fills its search tile (2, 4, 8, 12 or 16), K >= 8 and
+    n > 32; else 0. codes: uint64 [C][n] path digits (4 bits per level)."""
+    import numpy as np
+    codes = np.asarray(codes, dtype=np.uint64)
+    C = codes.shape[0]
+    tile = 2 if K <= 2 else 4 if K <= 4 else 8 if K <= 8 else 12 if K <= 12 else 16
+    lvl = lambda l: 1 + l
+    total = 0.0
+    for c in range(C):
+        T, npf = 0, n
+        if K == tile and K >= 8 and n > 32:
+            for t in (3, 2, 1):
+                npre = len(np.unique(codes[c] >> np.uint64(4 * (K - t))))
+                if npre <= 32:
+                    T, npf = t, npre
+                    break
+        shared = sum(lvl(l) for l in range(K - T + 1, K + 1))
+        rest = sum(lvl(l) for l in range(1, K - T + 1))
+        total += npf * shared + n * rest
+    return K * M + K * K + total / max(C, 1)
 
 
 class ClockSampler:
@@ -188,13 +216,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, budget_s: float = 10.0) -> dict:
+def cpu_baseline(w, budget_s: float = 10.0, gpu_sample=None) -> dict:
     """The oracle on whole slots of the workload (independent draws) until
-    about budget_s seconds of wall time have been spent, all host cores."""
+    about budget_s seconds of wall time have been spent, all host cores; then
+    on one core, on the leading channels of one slot, doubled until one run
+    takes budget_s / 8 seconds. gpu_sample = (batch, x, l,
+    gamma) of the timed GPU slot: the oracle recomputes 24 of its channels and
+    the line reports the agreement."""
+    import numpy as np
+
     from oracle import oracle as O
     from paper_2602_12098_gb300 import workloads as W
     threads = os.cpu_count() or 1
     O.build()
+    parity = None
+    if gpu_sample is not None:
+        b, x, l, g = gpu_sample
+        rng = np.random.default_rng(5)
+        C = b.H.shape[0]
+        chans = np.sort(rng.choice(C, min(24, C), replace=False))
+        vecs = np.concatenate([np.arange(b.vec_off[c], b.vec_off[c + 1]) for c in chans])
+        off = np.concatenate([[0], np.cumsum(np.diff(b.vec_off)[chans])]).astype(np.int32)
+        ref = O.precode_batch(b.H[chans], b.sym[vecs], off, w.qam, w.n_paths, nthreads=threads)
+        leq = np.all(l[vecs] == ref["l"], axis=(1, 2))
+        m = leq & (ref["gamma"] > 0)
+        parity = {"channels": int(len(chans)), "vectors": int(len(vecs)), "l_match": float(leq.mean()),
+                  "gamma_rel_max": float(np.max(np.abs(g[vecs][m] - ref["gamma"][m]) / ref["gamma"][m])),
+                  "x_err_max": float(np.max(np.linalg.norm(x[vecs][m] - ref["x"][m], axis=1))),
+                  "note": "where l matches; the GPU parity tests treat l differences (near-ties)"}
     V = 0
     dt = 0.0
     slots = 0
@@ -206,9 +255,22 @@ def cpu_baseline(w, budget_s: float = 10.0) -> dict:
         V += b.sym.shape[0]
         slots += 1
     cores = min(threads, O.max_threads()) if O.max_threads() > 1 else 1
-    return {"value": V / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{slots} whole slot(s) of {w.subcarriers} subcarriers x {w.symbols} symbols ({V} vectors), "
-                      f"{dt:.1f} s wall"}
+    # one core: leading channels of one slot, grown until ~budget_s / 4
+    sub_c, dt1, V1 = 8, 0.0, 0
+    while dt1 < budget_s / 8 and sub_c <= w.subcarriers:
+        b1 = W.make_batch(w, slot=100, subcarriers=sub_c)
+        t0 = time.perf_counter()
+        O.precode_batch(b1.H, b1.sym, b1.vec_off, w.qam, w.n_paths, nthreads=1)
+        dt1 = time.perf_counter() - t0
+        V1 = b1.sym.shape[0]
+        sub_c *= 2
+    out = {"value": V / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{slots} whole slot(s) of {w.subcarriers} subcarriers x {w.symbols} symbols ({V} vectors), "
+                     f"{dt:.1f} s wall",
+           "one_core": {"value": V1 / dt1, "unit": UNIT, "sample": f"{V1} vectors, {dt1:.1f} s"}}
+    if parity is not None:
+        out["parity_sample"] = parity
+    return out
 
 
 def profiled_traffic(kernel_file: str) -> dict | None:
@@ -240,7 +302,7 @@ def profiled_traffic(kernel_file: str) -> dict | None:
         return None
 
 
-def measure_batched(dev, flush) -> dict:
+def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
     """Uneven batch: 20,000 problems x 14 vectors, (K x M, Q, n) uniform over
     {4x8, 8x16, 12x16, 16x16} x {16, 64, 256} x {16, 64, 256, 1024}. Three
     ways: the grouped launches of vp_batch_launch, the same captured in a
@@ -252,7 +314,7 @@ def measure_batched(dev, flush) -> dict:
     import paper_2602_12098_gb300 as vp
     from paper_2602_12098_gb300 import workloads as W
     stream = torch.cuda.Stream(device=dev)      # graph capture needs a non-default stream
-    probs = W.uneven_problems(20000)
+    probs = W.uneven_problems(20000, symbols_per_problem=symbols_per_problem)
     pk = W.pack_problems(probs)
     V = int(pk.S.sum())
     H = torch.from_numpy(pk.H).to(dev)
@@ -261,8 +323,8 @@ def measure_batched(dev, flush) -> dict:
     l = torch.empty(pk.l_size, dtype=torch.int8, device=dev)
     g = torch.empty(pk.g_size, dtype=torch.float32, device=dev)
     descs = vp.packed_descs(pk, H, sym, x, l, g)
-    out = {"workload": "20000 problems x 14 vectors, (K x M, Q, n) uniform over {4x8, 8x16, 12x16, 16x16} x "
-                       "{16, 64, 256} x {16, 64, 256, 1024}, iid channels", "vectors": V}
+    out = {"workload": f"20000 problems x {symbols_per_problem} vector(s), (K x M, Q, n) uniform over "
+                       "{4x8, 8x16, 12x16, 16x16} x {16, 64, 256} x {16, 64, 256, 1024}, iid channels", "vectors": V}
 
     def timed(fn, reps):
         ts = []
@@ -426,7 +488,48 @@ def measure_fixed(dev, b, w, flush, steps: int, fracs=(8, 9, 10, 11, 12, 13)) ->
     return out
 
 
-def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 256) -> dict:
+def measure_paper_points(dev, flush, steps: int) -> list:
+    """The shapes of the paper's FPGA throughput table (K = M = 4, 8, 12, 16,
+    16-QAM) as whole slots with 8 paths: vectors/s of vp_factorize +
+    vp_precode, device-resident, L2 flushed between steps. The FPGA's figures
+    (one vector per clock: 424, 410, 264, 256 M vectors/s) are context."""
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    from paper_2602_12098_gb300 import workloads as W
+    fpga = {4: 424e6, 8: 410e6, 12: 264e6, 16: 256e6}
+    stream = torch.cuda.current_stream()
+    res = []
+    for w in W.PAPER_POINTS:
+        b = W.make_batch(w)
+        C, K, M = b.H.shape
+        V, S = b.sym.shape[0], w.symbols
+        H, sym = torch.from_numpy(b.H).to(dev), torch.from_numpy(b.sym).to(dev)
+        x = torch.empty((V, M), dtype=torch.complex64, device=dev)
+        l = torch.empty((V, K, 2), dtype=torch.int8, device=dev)
+        g = torch.empty((V,), dtype=torch.float32, device=dev)
+        with vp.Plan(K, M, w.qam, w.n_paths) as plan:
+            for _ in range(3):
+                vp.vp_factorize(plan.handle, H, C, stream=stream)
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, g, stream=stream)
+            ts = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vp.vp_factorize(plan.handle, H, C, stream=stream)
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, g, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        res.append({"workload": w.name, "slot_ms": ms, "vectors_per_s": V / (ms / 1e3),
+                    "fpga_vectors_per_s": fpga[K], "fpga_note": "paper's FPGA (16-bit fixed point, "
+                    "one vector per clock), context only"})
+    return res
+
+
+def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 256, n_paths: int = 64) -> dict:
     """Open-loop serving through the job server (vp_server_*): Poisson job
     arrivals (mean 4 per 0.5 ms slot); a job is one cell's slot, 3276
     subcarriers x 14 symbols, K in {4, 8, 12, 16}, M = 16, Q in {16, 64, 256},
@@ -441,7 +544,7 @@ def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 256) -> d
 
     import paper_2602_12098_gb300 as vp
     from paper_2602_12098_gb300 import workloads as W
-    jobs = W.poisson_jobs(n_slots)
+    jobs = W.poisson_jobs(n_slots, n_paths=n_paths)
     types = sorted({(j.K, j.M, j.qam, j.n_paths) for j in jobs})
     bufs = {}
     for t in types:
@@ -491,7 +594,7 @@ def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 256) -> d
     end = max(rec[3] for rec in done.values())
     vecs = sum(v for _, v in arrive.values())
     return {"workload": f"Poisson arrivals, mean 4 jobs per 0.5 ms slot, {n_slots} slots; job = 3276 subcarriers "
-                        "x 14 symbols, K in {4,8,12,16}, M 16, Q in {16,64,256}, n 64, iid",
+                        f"x 14 symbols, K in {{4,8,12,16}}, M 16, Q in {{16,64,256}}, n {n_paths}, iid",
             "engine": f"vp_server: {lanes} lanes (streams), {pool_mib} MiB state pool, first come first served "
                       "admission by idle lane and pool space",
             "jobs": len(jobs), "p50_job_ms": float(np.percentile(lat, 50)), "p99_job_ms": float(np.percentile(lat, 99)),
@@ -618,6 +721,15 @@ def run_gpu(args):
     flops_launch = paper_work_flops(K, M, w.n_paths) * V
     search_avg = statistics.mean(srch_ms)
     achieved = flops_launch / (search_avg / 1e3) / 1e12
+    # the state of the timed slot: FP64 channels and the paths (outside the timed region)
+    stt = torch.empty((C,), dtype=torch.uint8, device=dev)
+    vp.vp_factorize(h, H, C, None, None, None, stt, stream=stream)
+    codes = torch.empty((C, w.n_paths), dtype=torch.int64, device=dev)
+    vp.vp_get_paths(h, codes, stream=stream)
+    torch.cuda.synchronize()
+    fp64_frac = float((stt.cpu().numpy() & vp.VP_CH_FP64).astype(bool).mean())
+    exec_flops = 8.0 * executed_cmul(codes.cpu().numpy().view(np.uint64), K, M, w.n_paths) * V
+    executed = exec_flops / (search_avg / 1e3) / 1e12
     tr = profiled_traffic("search_kernel_slot16x16.md") if args.subcarriers is None else None
     roofline = {"bound": "alu", "kernel": "search_kernel<16> (vp_precode)", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
@@ -626,13 +738,17 @@ def run_gpu(args):
                                   if tr else "no ncu capture of the current search kernel sources"),
                 "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz "
                               "(max SM clock, MEASURED_PEAKS.json)",
-                "work_basis": "paper's per-vector complex-multiplication count x 8 flops"}
+                "work_basis": "paper's per-vector complex-multiplication count x 8 flops (effective: every "
+                              "path's full descent)",
+                "executed": executed, "executed_frac": executed / peak_tflops,
+                "executed_basis": "the same count with the shared top levels once per distinct prefix, as run"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "K": K, "M": M, "qam": w.qam, "n_paths": w.n_paths,
                        "channels": C, "vectors_per_step": V, "parallelism": f"replicas x{ws}",
+                       "fp64_channels_frac": fp64_frac,
                        "l2": "flushed between steps (256 MiB device write outside the timed events)"},
             "p50_slot_ms": statistics.median(step_ms),
             "p99_slot_ms": sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
@@ -643,10 +759,14 @@ def run_gpu(args):
         line["demap_lut"] = measure_lut(dev, b, w, flush, min(args.steps, 100))
         line["fixed_point"] = measure_fixed(dev, b, w, flush, min(args.steps, 20))
         line["batched"] = measure_batched(dev, flush)
+        line["batched_one_vector"] = measure_batched(dev, flush, symbols_per_problem=1)
+        line["paper_points"] = measure_paper_points(dev, flush, min(args.steps, 50))
     if ws == 1 and not args.no_serving:
-        line["serving"] = measure_serving(dev, args.serving_slots, args.serving_lanes, args.serving_pool_mib)
+        line["serving"] = measure_serving(dev, args.serving_slots, args.serving_lanes, args.serving_pool_mib,
+                                          args.serving_paths)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"] = cpu_baseline(w, gpu_sample=(b, x.cpu().numpy(), l.cpu().numpy(),
+                                                           g.cpu().numpy().astype(np.float64)))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -127,22 +127,14 @@ __device__ __forceinline__ void rank_cell(float D1x, float D2x, float D1y, float
     if (rA == k) { ci = 1; cj = 0; }
 }
 
-// t for rank q at effective point (cx, cy); `mq` = the warp's largest q at this
-// level (uniform) picks the cheapest branch that is exact for every lane. The
-// branches only choose the cell (ci, cj). Per axis the points in increasing
-// distance are n0 (the clamped rounding), s - n0 and -s, s = +1 for x > 0
-// else -1 (the three points of {-1, 0, 1} sum to zero).
-__device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, int& tr, int& ti,
-                                             float epsx = kEpsX, float epsy = kEpsY)
+// Cell (ci | cj << 2) of rank q at the shifted point (px, py) for a warp whose
+// largest q at this level (`mq`, uniform) is >= 1; the branch on mq picks the
+// cheapest form that is exact for every lane. Out of line on purpose: the
+// level bodies are unrolled 16 times, and keeping these rarer branches out
+// of them keeps the kernel's hot code within the instruction cache (inlined,
+// the search ran 9% slower on GB300).
+__device__ __noinline__ int select_cell(float px, float py, int q, int mq)
 {
-    const float px = cx - epsx, py = cy - epsy;
-    const int n0x = (px > 0.5f) - (px <= -0.5f);
-    const int n0y = (py > 0.5f) - (py <= -0.5f);
-    if (mq == 0) {
-        tr = n0x;
-        ti = n0y;
-        return;
-    }
     const float D1x = gap1(px), D1y = gap1(py);
     const bool f0 = D1x < D1y;                                        // rank 1: A (step in x) or B
     int ci, cj;
@@ -162,6 +154,26 @@ __device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, 
             if (q == 0) { ci = 0; cj = 0; }
         }
     }
+    return ci | (cj << 2);
+}
+
+// t for rank q at effective point (cx, cy); `mq` = the warp's largest q at
+// this level (uniform): 0 needs only the nearest point. The cells are chosen
+// per axis among n0 (the clamped rounding), s - n0 and -s, s = +1 for x > 0
+// else -1 (the three points of {-1, 0, 1} sum to zero).
+__device__ __forceinline__ void select_point(float cx, float cy, int q, int mq, int& tr, int& ti,
+                                             float epsx = kEpsX, float epsy = kEpsY)
+{
+    const float px = cx - epsx, py = cy - epsy;
+    const int n0x = (px > 0.5f) - (px <= -0.5f);
+    const int n0y = (py > 0.5f) - (py <= -0.5f);
+    if (mq == 0) {
+        tr = n0x;
+        ti = n0y;
+        return;
+    }
+    const int cc = select_cell(px, py, q, mq);
+    const int ci = cc & 3, cj = cc >> 2;
     const int sx = px > 0.f ? 1 : -1, sy = py > 0.f ? 1 : -1;
     tr = ci == 0 ? n0x : (ci == 1 ? sx - n0x : -sx);
     ti = cj == 0 ? n0y : (cj == 1 ? sy - n0y : -sy);
@@ -249,6 +261,21 @@ __device__ __forceinline__ void level_step(int lv, const float4* utp, const floa
             }
         }
     }
+}
+
+// One level's term of y = P u with P = ph + pl (hi + lo pair, user order):
+// exact products and compensated sums (u holds small integers, so P u keeps
+// ~48 bits before the final rounding).
+__device__ __forceinline__ void py_acc(const float2* pt, const float2* ptl, int idx, float ur, float ui, float& yr,
+                                       float& yre, float& yi, float& yie)
+{
+    const float2 ph = pt[idx], pl = ptl[idx];
+    dot2_acc(ph.x, ur, yr, yre);
+    dot2_acc(-ph.y, ui, yr, yre);
+    dot2_acc(ph.x, ui, yi, yie);
+    dot2_acc(ph.y, ur, yi, yie);
+    yre = fmaf(pl.x, ur, fmaf(-pl.y, ui, yre));
+    yie = fmaf(pl.x, ui, fmaf(pl.y, ur, yie));
 }
 
 __host__ __device__ inline int take16(int& o, int bytes)
@@ -402,125 +429,150 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     float* scrp = scrp_all + warp * kMaxPrefix;
     uint2* scrl = scrl_all + warp * kMaxPrefix;
     const int KB = K - T;   // levels evaluated per path
-    for (int v = v0 + warp; v < v1; v += NW) {
-        // symbols in level order (lane k <-> level k) and b_k = s_k + sum_{m>k} U~_km s_m
-        float2 s = make_float2(0.f, 0.f);
-        if (lane < K) s = qam_point((int)sym[(size_t)v * K + ulv[lane]], m_qam);
-        float2 b = s;
-        for (int m = 1; m < K; ++m) {
-            const float2 sm = make_float2(__shfl_sync(kFull, s.x, m), __shfl_sync(kFull, s.y, m));
-            if (lane < m) b = cfma(utc[m * KT + lane], sm, b);
-        }
-        // residuals are kept in units of tau: r' = r / tau is the effective point of Eq. (17)
-        b = make_float2(b.x * inv_tau, b.y * inv_tau);
-        if (FIX) b = make_float2(qword(b.x, fx), qword(b.y, fx));
-        if (lane < KT) bw[lane] = (lane < K) ? b : make_float2(0.f, 0.f);
-        float g0 = (lane < K) ? wv[lane] * cabs2(b) : 0.f;     // zero candidate: ||U s||^2
+    // The warp takes its vectors in pairs (v, v + NW): both are searched in
+    // turn, then one pass forms y = P u for both, one half-warp each (when the
+    // Mp rows fit 16 lanes; else each vector gets a whole-warp pass).
+    const bool pair_rows = Mp <= 16;
+    for (int v = v0 + warp; v < v1; v += 2 * NW) {
+        float2 upk = make_float2(0.f, 0.f);   // u of the pair: lanes 0-15 levels of v, lanes 16-31 of v + NW
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int vh = v + h * NW;
+            if (vh >= v1) break;
+            // symbols in level order (lane k <-> level k) and b_k = s_k + sum_{m>k} U~_km s_m
+            float2 s = make_float2(0.f, 0.f);
+            if (lane < K) s = qam_point((int)sym[(size_t)vh * K + ulv[lane]], m_qam);
+            float2 b = s;
+            for (int m = 1; m < K; ++m) {
+                const float2 sm = make_float2(__shfl_sync(kFull, s.x, m), __shfl_sync(kFull, s.y, m));
+                if (lane < m) b = cfma(utc[m * KT + lane], sm, b);
+            }
+            // residuals are kept in units of tau: r' = r / tau is the effective point of Eq. (17)
+            b = make_float2(b.x * inv_tau, b.y * inv_tau);
+            if (FIX) b = make_float2(qword(b.x, fx), qword(b.y, fx));
+            if (lane < KT) bw[lane] = (lane < K) ? b : make_float2(0.f, 0.f);
+            float g0 = (lane < K) ? wv[lane] * cabs2(b) : 0.f;     // zero candidate: ||U s||^2
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) g0 += __shfl_xor_sync(kFull, g0, o);
-        __syncwarp(kFull);
+            for (int o = 16; o >= 1; o >>= 1) g0 += __shfl_xor_sync(kFull, g0, o);
+            __syncwarp(kFull);
 
-        // shared top levels, one lane per prefix (T = 0: lane 0 stores the root state)
-        {
-            const uint64_t code = lane < NPF ? pcode[lane] : 0ull;
-            const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
-            float2 r[KT];
+            // shared top levels, one lane per prefix (T = 0: lane 0 stores the root state)
+            {
+                const uint64_t code = lane < NPF ? pcode[lane] : 0ull;
+                const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
+                float2 r[KT];
 #pragma unroll
-            for (int m = 0; m < KT; ++m) r[m] = bw[m];
-            float ped = 0.f;
-            uint32_t lc0 = 0, lc1 = 0;
-            constexpr int kLo = KT >= 8 ? KT - kSplitMax : KT;   // no shared levels for small tiles
+                for (int m = 0; m < KT; ++m) r[m] = bw[m];
+                float ped = 0.f;
+                uint32_t lc0 = 0, lc1 = 0;
+                constexpr int kLo = KT >= 8 ? KT - kSplitMax : KT;   // no shared levels for small tiles
 #pragma unroll
-            for (int lv = KT - 1; lv >= kLo; --lv) {
-                if (lv >= KT - T)
-                    level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, fx,
-                                             r, ped, lc0, lc1);
+                for (int lv = KT - 1; lv >= kLo; --lv) {
+                    if (lv >= KT - T)
+                        level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, fx,
+                                                 r, ped, lc0, lc1);
+                }
+                if (lane < NPF) {
+#pragma unroll
+                    for (int m = 0; m < KT; ++m)
+                        if (m < KB) scr[m * kMaxPrefix + lane] = r[m];
+                    scrp[lane] = ped;
+                    scrl[lane] = make_uint2(lc0, lc1);
+                }
             }
-            if (lane < NPF) {
-#pragma unroll
-                for (int m = 0; m < KT; ++m)
-                    if (m < KB) scr[m * kMaxPrefix + lane] = r[m];
-                scrp[lane] = ped;
-                scrl[lane] = make_uint2(lc0, lc1);
-            }
-        }
-        __syncwarp(kFull);
+            __syncwarp(kFull);
 
-        float bp = INFINITY;
-        int brk = 0x7fffffff;
-        uint32_t blc0 = 0, blc1 = 0;
-        for (int ch = 0; ch < nch; ++ch) {
-            const int jp = ch * 32 + lane;
-            const bool vld = jp < n;
-            const uint64_t code = vld ? tc[jp] : 0ull;
-            const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
-            const uint32_t mt = vld ? meta[jp] : 0u;
-            const int rk = vld ? (int)(mt & 0xffffu) : 0x7fffffff;
-            const int p = (int)(mt >> 16);
-            const uint64_t mq = tmq[ch];
-            float2 r[KT];
+            float bp = INFINITY;
+            int brk = 0x7fffffff;
+            uint32_t blc0 = 0, blc1 = 0;
+            for (int ch = 0; ch < nch; ++ch) {
+                const int jp = ch * 32 + lane;
+                const bool vld = jp < n;
+                const uint64_t code = vld ? tc[jp] : 0ull;
+                const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
+                const uint32_t mt = vld ? meta[jp] : 0u;
+                const int rk = vld ? (int)(mt & 0xffffu) : 0x7fffffff;
+                const int p = (int)(mt >> 16);
+                const uint64_t mq = tmq[ch];
+                float2 r[KT];
 #pragma unroll
-            for (int m = 0; m < KT; ++m) r[m] = (m < KB) ? scr[m * kMaxPrefix + p] : make_float2(0.f, 0.f);
-            float ped = scrp[p];
-            const uint2 lcp = scrl[p];
-            uint32_t lc0 = lcp.x, lc1 = lcp.y;
+                for (int m = 0; m < KT; ++m) r[m] = (m < KB) ? scr[m * kMaxPrefix + p] : make_float2(0.f, 0.f);
+                float ped = scrp[p];
+                const uint2 lcp = scrl[p];
+                uint32_t lc0 = lcp.x, lc1 = lcp.y;
 #pragma unroll
-            for (int lv = KT - 1; lv >= 0; --lv) {
-                if (lv < KB)
-                    level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, fx,
-                                             r, ped, lc0, lc1);
+                for (int lv = KT - 1; lv >= 0; --lv) {
+                    if (lv < KB)
+                        level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, fx,
+                                                 r, ped, lc0, lc1);
+                }
+                if (vld && (ped < bp || (ped == bp && rk < brk))) { bp = ped; brk = rk; blc0 = lc0; blc1 = lc1; }
             }
-            if (vld && (ped < bp || (ped == bp && rk < brk))) { bp = ped; brk = rk; blc0 = lc0; blc1 = lc1; }
-        }
-        // (PED, rank) minimum over the warp; candidate index = rank + 1
-        float wbp = bp;
-        int wbr = brk;
+            // (PED, rank) minimum over the warp; candidate index = rank + 1
+            float wbp = bp;
+            int wbr = brk;
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const float obp = __shfl_xor_sync(kFull, wbp, o);
-            const int obr = __shfl_xor_sync(kFull, wbr, o);
-            if (obp < wbp || (obp == wbp && obr < wbr)) { wbp = obp; wbr = obr; }
-        }
-        const bool zero_wins = !(wbp < g0);
-        const unsigned who = __ballot_sync(kFull, bp == wbp && brk == wbr);
-        const int src = (zero_wins || who == 0u) ? 0 : (__ffs(who) - 1);
-        uint32_t w0 = __shfl_sync(kFull, blc0, src), w1 = __shfl_sync(kFull, blc1, src);
-        if (zero_wins) { w0 = 0x55555555u; w1 = 0x55555555u; }
+            for (int o = 16; o >= 1; o >>= 1) {
+                const float obp = __shfl_xor_sync(kFull, wbp, o);
+                const int obr = __shfl_xor_sync(kFull, wbr, o);
+                if (obp < wbp || (obp == wbp && obr < wbr)) { wbp = obp; wbr = obr; }
+            }
+            const bool zero_wins = !(wbp < g0);
+            const unsigned who = __ballot_sync(kFull, bp == wbp && brk == wbr);
+            const int src = (zero_wins || who == 0u) ? 0 : (__ffs(who) - 1);
+            uint32_t w0 = __shfl_sync(kFull, blc0, src), w1 = __shfl_sync(kFull, blc1, src);
+            if (zero_wins) { w0 = 0x55555555u; w1 = 0x55555555u; }
 
-        // l (user order) and u = s + tau l = s - tau t in level order
-        float2 u = make_float2(0.f, 0.f);
-        if (lane < K) {
-            const int nib = (int)(((lane < 8 ? w0 : w1) >> (4 * (lane & 7))) & 15u);
-            const int tr = (nib & 3) - 1, ti = (nib >> 2) - 1;
-            u = make_float2(s.x - (float)tr * tau, s.y - (float)ti * tau);
-            const int usr = ulv[lane];
-            lo[((size_t)v * K + usr) * 2] = (int8_t)(-tr);
-            lo[((size_t)v * K + usr) * 2 + 1] = (int8_t)(-ti);
-        }
-        // y = P u with P = pt + ptl: exact products and compensated sums (u holds
-        // small integers, so P u keeps ~48 bits before the final rounding)
-        float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
-        for (int lv = 0; lv < K; ++lv) {
-            const float ur = __shfl_sync(kFull, u.x, lv), ui = __shfl_sync(kFull, u.y, lv);
-            if (lane < Mp) {
-                const int idx = ulv[lv] * Mp + lane;
-                const float2 ph = pt[idx], pl = ptl[idx];
-                dot2_acc(ph.x, ur, yr, yre);
-                dot2_acc(-ph.y, ui, yr, yre);
-                dot2_acc(ph.x, ui, yi, yie);
-                dot2_acc(ph.y, ur, yi, yie);
-                yre = fmaf(pl.x, ur, fmaf(-pl.y, ui, yre));
-                yie = fmaf(pl.x, ui, fmaf(pl.y, ur, yie));
+            // l (user order) and u = s + tau l = s - tau t in level order
+            float2 u = make_float2(0.f, 0.f);
+            if (lane < K) {
+                const int nib = (int)(((lane < 8 ? w0 : w1) >> (4 * (lane & 7))) & 15u);
+                const int tr = (nib & 3) - 1, ti = (nib >> 2) - 1;
+                u = make_float2(s.x - (float)tr * tau, s.y - (float)ti * tau);
+                const int usr = ulv[lane];
+                lo[((size_t)vh * K + usr) * 2] = (int8_t)(-tr);
+                lo[((size_t)vh * K + usr) * 2 + 1] = (int8_t)(-ti);
             }
-        }
-        const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
-        float g = (lane < Mp) ? cabs2(y) : 0.f;     // ||w||^2 over all rows (Alg. 2's d)
+            if (pair_rows) {
+                const float ux = __shfl_sync(kFull, u.x, lane & 15), uy = __shfl_sync(kFull, u.y, lane & 15);
+                if ((lane >> 4) == h) upk = make_float2(ux, uy);
+                __syncwarp(kFull);
+                continue;
+            }
+            // y = P u with P = pt + ptl, all Mp rows on the warp
+            float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
+            for (int lv = 0; lv < K; ++lv) {
+                const float ur = __shfl_sync(kFull, u.x, lv), ui = __shfl_sync(kFull, u.y, lv);
+                if (lane < Mp) py_acc(pt, ptl, ulv[lv] * Mp + lane, ur, ui, yr, yre, yi, yie);
+            }
+            const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
+            float g = (lane < Mp) ? cabs2(y) : 0.f;     // ||w||^2 over all rows (Alg. 2's d)
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
-        const float rs = __frsqrt_rn(g);
-        if (lane < M) xo[(size_t)v * M + lane] = make_float2(y.x * rs, y.y * rs);
-        if (lane == 0) go[v] = g;
-        __syncwarp(kFull);
+            for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
+            const float rs = __frsqrt_rn(g);
+            if (lane < M) xo[(size_t)vh * M + lane] = make_float2(y.x * rs, y.y * rs);
+            if (lane == 0) go[vh] = g;
+            __syncwarp(kFull);
+        }
+        if (pair_rows) {
+            // y = P u for the pair: half-warp hf forms the rows of vector v + hf NW
+            const int hf = lane >> 4, m = lane & 15;
+            const int vh = v + hf * NW;
+            const bool on = vh < v1 && m < Mp;
+            float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
+            for (int lv = 0; lv < K; ++lv) {
+                const float ur = __shfl_sync(kFull, upk.x, lv + 16 * hf), ui = __shfl_sync(kFull, upk.y, lv + 16 * hf);
+                if (on) py_acc(pt, ptl, ulv[lv] * Mp + m, ur, ui, yr, yre, yi, yie);
+            }
+            const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
+            float g = on ? cabs2(y) : 0.f;              // ||w||^2 over all rows (Alg. 2's d)
+#pragma unroll
+            for (int o = 8; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
+            const float rs = __frsqrt_rn(g);
+            if (vh < v1 && m < M) xo[(size_t)vh * M + m] = make_float2(y.x * rs, y.y * rs);
+            if (vh < v1 && m == 0) go[vh] = g;
+            __syncwarp(kFull);
+        }
     }
 }
 

@@ -62,6 +62,12 @@ SLOT_16x16 = Workload("16x16 256-QAM, 3276 subcarriers x 14 symbols (100 MHz slo
                       channel="kron", rho_ap=0.5, rho_u=0.2, seed_offset=2)
 WORKLOADS = {"small_4x4": SMALL_4x4, "rb_8x8": RB_8x8, "slot_16x16": SLOT_16x16}
 
+# The shapes of the paper's accelerator throughput table (Table II: K = M in
+# {4, 8, 12, 16}, 16-QAM), here as whole 100 MHz slots with 8 paths, iid.
+PAPER_POINTS = [Workload(f"{k}x{k} 16-QAM, 3276 subcarriers x 14 symbols, 8 paths, iid", K=k, M=k, qam=16,
+                         n_paths=8, subcarriers=3276, symbols=14, channel="iid", seed_offset=6)
+                for k in (4, 8, 12, 16)]
+
 
 def rng_for(seed_offset: int, stream: int = 0) -> np.random.Generator:
     """PCG64 generator for a workload (base seed + offset) and a sub-stream."""
