@@ -451,13 +451,20 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
             }
             if (!(key > 1e-12 * dmax)) { singular = true; break; }      // uniform across the warp
             const int p = ku;
-            const double rt = sqrt(key), irt = 1.0 / rt;
+            // 1 / sqrt(key): FP32 estimate, two Newton steps in FP64 (y <- y (3 - k y^2) / 2,
+            // each doubling the correct bits), then sqrt(key) = key / sqrt(key)
+            double irt = (double)rsqrtf((float)key);
+            if (!(irt > 0.0 && irt < INFINITY)) irt = 1.0 / sqrt(key);   // key outside the FP32 range
+            irt = irt * (1.5 - 0.5 * key * irt * irt);
+            irt = irt * (1.5 - 0.5 * key * irt * irt);
+            const double rt = key * irt;
             // remove p from the remaining list (move the last one into its position)
             const int last = sm.rem[m - 1];
             __syncwarp();
             if (lane == 0) {
                 sm.rem[kp] = last;
                 sm.rd[t] = rt;
+                sm.rinv[t] = irt;
                 sm.uol[t] = p;
             }
             __syncwarp();
@@ -485,7 +492,6 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 const int r = e / K, q = e % K;
                 sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
             }
-            if (lane < K) sm.rinv[lane] = 1.0 / sm.rd[lane];
             __syncwarp();
             for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = make_double2(0.0, 0.0);
             __syncwarp();
@@ -533,14 +539,16 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 __syncwarp();
             }
             // U2 (in lc) as FP32 hi + lo; outputs: row r of U~, w_r, user of level r
+            if (lane < K) sm.rd[lane] = 1.0 / sm.lc[lane][lane].x;     // 1 / U2_rr
+            __syncwarp();
             for (int e = lane; e < K * K; e += 32) {
                 const int r = e / K, q = e % K;
                 const double2 v = sm.lc[r][q];
                 const float hx = (float)v.x, hy = (float)v.y;
                 sm.uh[r][q] = make_float2(hx, hy);
                 sm.ul[r][q] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
-                const double urr = sm.lc[r][r].x;
-                const float2 ut = (q > r) ? make_float2((float)(v.x / urr), (float)(v.y / urr))
+                const double urr = sm.lc[r][r].x, iurr = sm.rd[r];
+                const float2 ut = (q > r) ? make_float2((float)(v.x * iurr), (float)(v.y * iurr))
                                           : (q == r ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
                 f.s.utp[r * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
                 f.s.utc[q * K + r] = ut;

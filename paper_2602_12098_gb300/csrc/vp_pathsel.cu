@@ -108,6 +108,92 @@ __host__ __device__ inline int pow2_ceil(int n)
 }
 __host__ __device__ inline size_t eval_order_bytes(int n) { return 12 * (size_t)pow2_ceil(n) + 8 + 1664; }
 
+// (key, val) pairs ordered by key, then val (padding entries are equal pairs)
+__device__ __forceinline__ bool kv_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb)
+{
+    return ka < kb || (ka == kb && va < vb);
+}
+
+// Ascending bitonic sort of key[0..np2) / val[0..np2) (np2 = E * tpc) held in
+// registers, E consecutive entries per thread (entry i = t E + e): partners
+// within a thread are compared in registers, within a warp through
+// shuffles, and across the group's warps through shared memory (key / val
+// are the staging area). The same network as the shared-memory sort.
+template <int E>
+__device__ void bitonic_regs(uint64_t* key, uint32_t* val, int np2, int t, int tpc)
+{
+    auto gsync = [&]() {
+        if (tpc == 32) __syncwarp(kFull);
+        else __syncthreads();
+    };
+    uint64_t k[E];
+    uint32_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        k[e] = key[t * E + e];
+        v[e] = val[t * E + e];
+    }
+    gsync();
+    for (int kk = 2; kk <= np2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j < E) {                                      // partner in the same thread
+#pragma unroll
+                for (int jj = E >> 1; jj >= 1; jj >>= 1) {    // compile-time distance: registers stay registers
+                    if (jj != j) continue;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int f = e ^ jj;
+                        if (f > e) {
+                            const int i = t * E + e;
+                            const bool up = (i & kk) == 0;
+                            if (kv_less(k[f], v[f], k[e], v[e]) == up) {
+                                const uint64_t tk = k[e]; k[e] = k[f]; k[f] = tk;
+                                const uint32_t tv = v[e]; v[e] = v[f]; v[f] = tv;
+                            }
+                        }
+                    }
+                }
+            } else {
+                const int tm = j / E;                         // partner thread t ^ tm
+                if (tm < 32) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int i = t * E + e;
+                        const uint64_t ok = __shfl_xor_sync(kFull, k[e], tm);
+                        const uint32_t ov = __shfl_xor_sync(kFull, v[e], tm);
+                        const bool up = (i & kk) == 0, low = (i & j) == 0;
+                        const bool other_less = kv_less(ok, ov, k[e], v[e]);
+                        if (other_less == (up == low)) { k[e] = ok; v[e] = ov; }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        key[t * E + e] = k[e];
+                        val[t * E + e] = v[e];
+                    }
+                    gsync();
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int i = t * E + e;
+                        const uint64_t ok = key[(t ^ tm) * E + e];
+                        const uint32_t ov = val[(t ^ tm) * E + e];
+                        const bool up = (i & kk) == 0, low = (i & j) == 0;
+                        const bool other_less = kv_less(ok, ov, k[e], v[e]);
+                        if (other_less == (up == low)) { k[e] = ok; v[e] = ov; }
+                    }
+                    gsync();
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        key[t * E + e] = k[e];
+        val[t * E + e] = v[e];
+    }
+    gsync();
+}
+
 __device__ void eval_order(const ChanState& cs, const uint64_t* out, uint64_t* base, int n, int K, int nch, int t,
                            int tpc)
 {
@@ -197,6 +283,13 @@ __device__ void eval_order(const ChanState& cs, const uint64_t* out, uint64_t* b
     }
     if (T == 0 && t == 0) pcs[0] = 0ull;
     gsync();
+    const int E = np2 / tpc;
+    if (nch > 1 && np2 >= tpc && E <= 8) {                       // ascending sort in registers
+        if (E == 1) bitonic_regs<1>(key, val, np2, t, tpc);
+        else if (E == 2) bitonic_regs<2>(key, val, np2, t, tpc);
+        else if (E == 4) bitonic_regs<4>(key, val, np2, t, tpc);
+        else bitonic_regs<8>(key, val, np2, t, tpc);
+    } else
     for (int k = 2; k <= (nch > 1 ? np2 : 1); k <<= 1) {         // ascending bitonic sort, keys distinct
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = t; i < (np2 >> 1); i += tpc) {
