@@ -278,6 +278,31 @@ __device__ __forceinline__ void py_acc(const float2* pt, const float2* ptl, int 
     yie = fmaf(pl.x, ui, fmaf(pl.y, ur, yie));
 }
 
+// y = P u, gamma = ||y||^2 and x = the antenna rows / sqrt(gamma) for two
+// vectors at once: half-warp hf takes vector hf ? vB : vA (Mp <= 16 rows);
+// upk holds u, lanes 0-15 by level for vA and lanes 16-31 for vB.
+__device__ __forceinline__ void pair_rows_out(const float2* pt, const float2* ptl, const int* ulv, float2 upk, int K,
+                                              int M, int Mp, int vA, int vB, int v1, float2* xo, float* go)
+{
+    const int lane = threadIdx.x & 31;
+    const int hf = lane >> 4, m = lane & 15;
+    const int vh = hf ? vB : vA;
+    const bool on = vh < v1 && m < Mp;
+    float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
+    for (int lv = 0; lv < K; ++lv) {
+        const float ur = __shfl_sync(kFull, upk.x, lv + 16 * hf), ui = __shfl_sync(kFull, upk.y, lv + 16 * hf);
+        if (on) py_acc(pt, ptl, ulv[lv] * Mp + m, ur, ui, yr, yre, yi, yie);
+    }
+    const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
+    float g = on ? cabs2(y) : 0.f;              // ||w||^2 over all rows (Alg. 2's d)
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
+    const float rs = __frsqrt_rn(g);
+    if (vh < v1 && m < M) xo[(size_t)vh * M + m] = make_float2(y.x * rs, y.y * rs);
+    if (vh < v1 && m == 0) go[vh] = g;
+    __syncwarp(kFull);
+}
+
 __host__ __device__ inline int take16(int& o, int bytes)
 {
     const int r = o;
@@ -554,26 +579,223 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
             if (lane == 0) go[vh] = g;
             __syncwarp(kFull);
         }
-        if (pair_rows) {
-            // y = P u for the pair: half-warp hf forms the rows of vector v + hf NW
-            const int hf = lane >> 4, m = lane & 15;
-            const int vh = v + hf * NW;
-            const bool on = vh < v1 && m < Mp;
-            float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
-            for (int lv = 0; lv < K; ++lv) {
-                const float ur = __shfl_sync(kFull, upk.x, lv + 16 * hf), ui = __shfl_sync(kFull, upk.y, lv + 16 * hf);
-                if (on) py_acc(pt, ptl, ulv[lv] * Mp + m, ur, ui, yr, yre, yi, yie);
+        if (pair_rows) pair_rows_out(pt, ptl, ulv, upk, K, M, Mp, v, v + NW, v1, xo, go);
+    }
+}
+
+// Shared-memory layout of the one-pass search (byte offsets, 16-byte aligned).
+struct SmallSmem {
+    int utp, utc, pt, ptl, tc, meta, wv, ulv, bw, sv, g0, wins, total;
+};
+
+__host__ __device__ inline SmallSmem small_smem(int KT, int KM, int NW, int G)
+{
+    SmallSmem s;
+    int o = 0;
+    s.utp = take16(o, 16 * KT * KT);
+    s.utc = take16(o, 8 * KT * KT);
+    s.pt = take16(o, 8 * KM);
+    s.ptl = take16(o, 8 * KM);
+    s.tc = take16(o, 8 * 32);
+    s.meta = take16(o, 4 * 32);
+    s.wv = take16(o, 4 * KT);
+    s.ulv = take16(o, 4 * KT);
+    s.bw = take16(o, 8 * NW * G * KT);
+    s.sv = take16(o, 8 * NW * G * KT);
+    s.g0 = take16(o, 4 * NW * G);
+    s.wins = take16(o, 8 * NW * G);
+    s.total = o;
+    return s;
+}
+
+// The search for path budgets of one pass (n <= 32 / G): G data vectors per
+// warp, P = 32 / G lanes each (lane g P + p: vector g, path p), so that small
+// budgets keep the lanes busy. The arithmetic per path and the (PED, rank)
+// argmin are those of search_kernel, which shares no levels when n <= 32,
+// and y = P u takes the same paired half-warp pass: the outputs are the same.
+template <int KT, int G>
+__global__ void __launch_bounds__(224, 4) search_small_kernel(SearchArgs a)
+{
+    constexpr int P = 32 / G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int NW = blockDim.x >> 5;
+    const int c = blockIdx.x;
+    const int K = a.K, M = a.M, Mp = a.Mp, n = a.n, m_qam = a.m_qam;
+    const float tau = a.tau, inv_tau = a.inv_tau;
+    int v0, v1;
+    if (a.off) {
+        v0 = min(max(a.off[c], 0), a.n_vec);
+        v1 = min(max(a.off[c + 1], v0), a.n_vec);
+    } else {
+        v0 = c * a.S;
+        v1 = v0 + a.S;
+    }
+    const ChanState cs = chan_state(a.d, (size_t)c, K, Mp, n);
+    const uint8_t* sym = a.sym;
+    float2* xo = a.x;
+    int8_t* lo = a.l;
+    float* go = a.gamma;
+    const SmallSmem L = small_smem(KT, K * Mp, NW, G);
+    float4* utp = reinterpret_cast<float4*>(smraw + L.utp);        // [KT][KT]
+    float2* utc = reinterpret_cast<float2*>(smraw + L.utc);        // [KT][KT]
+    float2* pt = reinterpret_cast<float2*>(smraw + L.pt);          // [K][Mp]
+    float2* ptl = reinterpret_cast<float2*>(smraw + L.ptl);
+    uint64_t* tc = reinterpret_cast<uint64_t*>(smraw + L.tc);      // [n] codes
+    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + L.meta);  // [n] MoP rank
+    float* wv = reinterpret_cast<float*>(smraw + L.wv);            // [KT]
+    int* ulv = reinterpret_cast<int*>(smraw + L.ulv);              // [KT]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* bw = reinterpret_cast<float2*>(smraw + L.bw) + warp * G * KT;   // [G][KT] b' of the warp's vectors
+    float2* sv = reinterpret_cast<float2*>(smraw + L.sv) + warp * G * KT;   // [G][KT] their symbols
+    float* g0s = reinterpret_cast<float*>(smraw + L.g0) + warp * G;         // [G] zero candidates
+    uint2* wins = reinterpret_cast<uint2*>(smraw + L.wins) + warp * G;      // [G] chosen points
+
+    if (cs.st[0] & (VP_CH_NONFINITE | VP_CH_SINGULAR)) {
+        for (int v = v0 + warp; v < v1; v += NW) {
+            if (lane < M) xo[(size_t)v * M + lane] = make_float2(0.f, 0.f);
+            if (lane < K) {
+                lo[((size_t)v * K + lane) * 2] = 0;
+                lo[((size_t)v * K + lane) * 2 + 1] = 0;
             }
-            const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
-            float g = on ? cabs2(y) : 0.f;              // ||w||^2 over all rows (Alg. 2's d)
+            if (lane == 0) go[v] = 0.f;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
+        const int r = i / KT, q = i % KT;
+        const bool in = r < K && q < K;
+        utp[i] = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        utc[i] = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
+        pt[i] = cs.pt[i];
+        ptl[i] = cs.ptlo[i];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tc[i] = cs.ecode[i];
+        meta[i] = cs.emeta[i];
+    }
+    for (int i = threadIdx.x; i < KT; i += blockDim.x) {
+        wv[i] = i < K ? cs.w[i] * tau * tau : 0.f;   // w_l tau^2
+        ulv[i] = i < K ? (int)cs.ul[i] : 0;
+    }
+    const uint64_t mq = cs.maxq[0];                   // one chunk: digit maxima of all paths
+    const FixP fx = FixP();
+    __syncthreads();
+
+    const int g = lane / P, p = lane % P;
+    for (int vb = v0 + warp * G; vb < v1; vb += NW * G) {
+        // b' and the zero candidate of each vector (lane k <-> level k)
+#pragma unroll 1
+        for (int h = 0; h < G; ++h) {
+            const int vh = vb + h;
+            if (vh >= v1) break;
+            float2 s = make_float2(0.f, 0.f);
+            if (lane < K) s = qam_point((int)sym[(size_t)vh * K + ulv[lane]], m_qam);
+            float2 b = s;
+            for (int m = 1; m < K; ++m) {
+                const float2 sm = make_float2(__shfl_sync(kFull, s.x, m), __shfl_sync(kFull, s.y, m));
+                if (lane < m) b = cfma(utc[m * KT + lane], sm, b);
+            }
+            b = make_float2(b.x * inv_tau, b.y * inv_tau);
+            if (lane < KT) {
+                bw[h * KT + lane] = (lane < K) ? b : make_float2(0.f, 0.f);
+                sv[h * KT + lane] = s;
+            }
+            float g0 = (lane < K) ? wv[lane] * cabs2(b) : 0.f;
 #pragma unroll
-            for (int o = 8; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
-            const float rs = __frsqrt_rn(g);
-            if (vh < v1 && m < M) xo[(size_t)vh * M + m] = make_float2(y.x * rs, y.y * rs);
-            if (vh < v1 && m == 0) go[vh] = g;
-            __syncwarp(kFull);
+            for (int o = 16; o >= 1; o >>= 1) g0 += __shfl_xor_sync(kFull, g0, o);
+            if (lane == 0) g0s[h] = g0;
+        }
+        __syncwarp(kFull);
+
+        // every path of every vector: lane (g, p)
+        const int vg = vb + g;
+        const bool vld = vg < v1 && p < n;
+        const uint64_t code = vld ? tc[p] : 0ull;
+        const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
+        const int rk = vld ? (int)(meta[p] & 0xffffu) : 0x7fffffff;
+        float2 r[KT];
+#pragma unroll
+        for (int m = 0; m < KT; ++m) r[m] = bw[g * KT + m];
+        float ped = 0.f;
+        uint32_t lc0 = 0, lc1 = 0;
+#pragma unroll
+        for (int lv = KT - 1; lv >= 0; --lv) {
+            if (lv < K)
+                level_step<KT, false, false>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), nullptr, fx,
+                                             r, ped, lc0, lc1);
+        }
+        const float bp = vld ? ped : INFINITY;
+        const int brk = rk;
+        float wbp = bp;
+        int wbr = brk;
+#pragma unroll
+        for (int o = P / 2; o >= 1; o >>= 1) {
+            const float obp = __shfl_xor_sync(kFull, wbp, o);
+            const int obr = __shfl_xor_sync(kFull, wbr, o);
+            if (obp < wbp || (obp == wbp && obr < wbr)) { wbp = obp; wbr = obr; }
+        }
+        const bool zero_wins = !(wbp < g0s[g]);
+        const unsigned gmask = (P == 32) ? kFull : (((1u << P) - 1u) << (g * P));
+        const unsigned who = __ballot_sync(kFull, bp == wbp && brk == wbr) & gmask;
+        const int src = (zero_wins || who == 0u) ? g * P : (__ffs(who) - 1);
+        uint32_t w0 = __shfl_sync(kFull, lc0, src), w1 = __shfl_sync(kFull, lc1, src);
+        if (zero_wins) { w0 = 0x55555555u; w1 = 0x55555555u; }
+        if (p == 0) wins[g] = make_uint2(w0, w1);
+        __syncwarp(kFull);
+
+        // l, u and y = P u, two vectors per pass
+#pragma unroll 1
+        for (int h0 = 0; h0 < G; h0 += 2) {
+            if (vb + h0 >= v1) break;
+            float2 upk = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int h = h0 + hh, vh = vb + h;
+                if (vh >= v1) break;
+                const uint2 wn = wins[h];
+                float2 u = make_float2(0.f, 0.f);
+                if (lane < K) {
+                    const int nib = (int)(((lane < 8 ? wn.x : wn.y) >> (4 * (lane & 7))) & 15u);
+                    const int tr = (nib & 3) - 1, ti = (nib >> 2) - 1;
+                    const float2 s = sv[h * KT + lane];
+                    u = make_float2(s.x - (float)tr * tau, s.y - (float)ti * tau);
+                    const int usr = ulv[lane];
+                    lo[((size_t)vh * K + usr) * 2] = (int8_t)(-tr);
+                    lo[((size_t)vh * K + usr) * 2 + 1] = (int8_t)(-ti);
+                }
+                const float ux = __shfl_sync(kFull, u.x, lane & 15), uy = __shfl_sync(kFull, u.y, lane & 15);
+                if ((lane >> 4) == hh) upk = make_float2(ux, uy);
+            }
+            pair_rows_out(pt, ptl, ulv, upk, K, M, Mp, vb + h0, vb + h0 + 1, v1, xo, go);
         }
     }
+}
+
+template <int KT, int G>
+cudaError_t launch_small(const SearchArgs& a, int C, int per, cudaStream_t s)
+{
+    int nw = (per + G - 1) / G;
+    nw = nw < 1 ? 1 : (nw > 7 ? 7 : nw);
+    const size_t sh = (size_t)small_smem(KT, a.K * a.Mp, nw, G).total;
+    static size_t attr = 0;
+    if (sh > 40 * 1024 && sh > attr) {
+        cudaError_t e = cudaFuncSetAttribute(search_small_kernel<KT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sh);
+        if (e != cudaSuccess) return e;
+        attr = sh;
+    }
+    search_small_kernel<KT, G><<<C, nw * 32, sh, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int KT>
+cudaError_t launch_small_kt(const SearchArgs& a, int C, int per, cudaStream_t s)
+{
+    if (a.n <= 4) return launch_small<KT, 8>(a, C, per, s);
+    if (a.n <= 8) return launch_small<KT, 4>(a, C, per, s);
+    return launch_small<KT, 2>(a, C, per, s);
 }
 
 template <int KT, bool BATCH, bool LUT, bool FIX>
@@ -641,6 +863,14 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     else if (per % 7 != 0 && per % 6 == 0) nw = 6;
     const int threads = nw * 32;
     const int K = p->K;
+    // budgets of 16 paths or fewer: several vectors per warp (same results)
+    if (a.n <= 16 && a.Mp <= 16 && a.demap == VP_DEMAP_EXACT && a.frac == 0 && per >= 2) {
+        if (K <= 2) return launch_small_kt<2>(a, p->C, per, s);
+        if (K <= 4) return launch_small_kt<4>(a, p->C, per, s);
+        if (K <= 8) return launch_small_kt<8>(a, p->C, per, s);
+        if (K <= 12) return launch_small_kt<12>(a, p->C, per, s);
+        return launch_small_kt<16>(a, p->C, per, s);
+    }
     if (K <= 2) return launch_kt<2>(a, p->C, threads, s);
     if (K <= 4) return launch_kt<4>(a, p->C, threads, s);
     if (K <= 8) return launch_kt<8>(a, p->C, threads, s);

@@ -187,3 +187,32 @@ def test_host_buffer_slot_equals_device_path():
     assert np.array_equal(xh.numpy(), dev["x"])
     assert np.array_equal(lh.numpy(), dev["l"])
     assert np.array_equal(gh.numpy().astype(np.float64), dev["gamma"])
+
+
+@pytest.mark.parametrize("K,M,qam,n,S", [(16, 16, 16, 8, 14), (8, 8, 64, 16, 14), (4, 4, 16, 4, 7), (12, 16, 256, 1, 30),
+                                         (2, 3, 64, 9, 2), (16, 16, 256, 16, 3)])
+def test_small_budgets_several_vectors_per_warp(orc, K, M, qam, n, S):
+    """Budgets of <= 16 paths run several data vectors per warp; against the
+    oracle, and bit-equal to the same problems through the uneven-batch path
+    (one vector per warp)."""
+    rng = W.rng_for(130, K * 1000 + n * 10 + S)
+    C = 40
+    H = W.channels(rng, C, K, M)
+    sym = W.symbols(rng, C * S, K, qam)
+    off = W.vec_offsets_uniform(C, S)
+    gpu = run_gpu(H, sym, off, qam, n, want_factor=False, uniform_S=S)
+    ref = orc.precode_batch(H, sym, off, qam, n, nthreads=orc.max_threads())
+    assert_parity(compare(orc, H, sym, off, qam, gpu, ref))
+    dev = torch.device("cuda:0")
+    probs = [W.Problem(K, M, qam, n, H[c], sym[c * S:(c + 1) * S]) for c in range(C)]
+    pk = W.pack_problems(probs)
+    Hd, sd = torch.from_numpy(pk.H).to(dev), torch.from_numpy(pk.sym).to(dev)
+    x = torch.empty(pk.x_size, dtype=torch.complex64, device=dev)
+    l = torch.empty(pk.l_size, dtype=torch.int8, device=dev)
+    g = torch.empty(pk.g_size, dtype=torch.float32, device=dev)
+    with vp.Batch(vp.packed_descs(pk, Hd, sd, x, l, g)) as bt:
+        bt.launch()
+        torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy().reshape(C * S, M), gpu["x"])
+    assert np.array_equal(l.cpu().numpy().reshape(C * S, K, 2), gpu["l"])
+    assert np.array_equal(g.cpu().numpy().astype(np.float64), gpu["gamma"])
