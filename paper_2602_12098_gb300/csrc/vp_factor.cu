@@ -440,15 +440,22 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
         bool singular = false;
         for (int t = K - 1; t >= 0; --t) {
             const int m = t + 1;                                       // remaining users before the pivot
-            double key = INFINITY;
+            // smallest diagonal: the doubles compared as ordered integers (sign-folded bit
+            // patterns), which keeps the comparisons off the FP64 pipe
+            long long ik = 0x7ff0000000000000ll;                        // +infinity
             int ku = 0x7fffffff, kp = lane;
-            if (lane < m) { ku = sm.rem[lane]; key = sm.s[ku][ku].x; }
+            if (lane < m) {
+                ku = sm.rem[lane];
+                const long long b = __double_as_longlong(sm.s[ku][ku].x);
+                ik = b ^ ((b >> 63) & 0x7fffffffffffffffll);
+            }
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
-                const double ok = __shfl_xor_sync(kFull, key, o);
+                const long long ok = __shfl_xor_sync(kFull, ik, o);
                 const int ou = __shfl_xor_sync(kFull, ku, o), op = __shfl_xor_sync(kFull, kp, o);
-                if (ok < key || (ok == key && ou < ku)) { key = ok; ku = ou; kp = op; }
+                if (ok < ik || (ok == ik && ou < ku)) { ik = ok; ku = ou; kp = op; }
             }
+            const double key = __longlong_as_double(ik ^ ((ik >> 63) & 0x7fffffffffffffffll));
             if (!(key > 1e-12 * dmax)) { singular = true; break; }      // uniform across the warp
             const int p = ku;
             // 1 / sqrt(key): FP32 estimate, two Newton steps in FP64 (y <- y (3 - k y^2) / 2,
