@@ -488,6 +488,55 @@ def measure_fixed(dev, b, w, flush, steps: int, fracs=(8, 9, 10, 11, 12, 13)) ->
     return out
 
 
+def measure_pipelined(dev, w, steps: int, n_inputs: int = 8) -> dict:
+    """Consecutive slots with overlap: two plans on two streams, so that slot
+    i + 1's vp_factorize runs beside slot i's vp_precode. Inputs rotate over
+    n_inputs independent slot draws (with the two plans' state the working set
+    exceeds L2, so no flush runs between slots). Reported beside the plain
+    per-slot line, which runs the slots one after another."""
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    from paper_2602_12098_gb300 import workloads as W
+    bs = [W.make_batch(w, slot=200 + i) for i in range(n_inputs)]
+    C, K, M = bs[0].H.shape
+    V, S = bs[0].sym.shape[0], w.symbols
+    Hs = [torch.from_numpy(b.H).to(dev) for b in bs]
+    Ss = [torch.from_numpy(b.sym).to(dev) for b in bs]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    plans = [vp.Plan(K, M, w.qam, w.n_paths) for _ in range(2)]
+    outs = [(torch.empty((V, M), dtype=torch.complex64, device=dev), torch.empty((V, K, 2), dtype=torch.int8, device=dev),
+             torch.empty((V,), dtype=torch.float32, device=dev)) for _ in range(2)]
+
+    def slot(i):
+        k = i % 2
+        vp.vp_factorize(plans[k].handle, Hs[i % n_inputs], C, stream=streams[k])
+        vp.vp_precode(plans[k].handle, Ss[i % n_inputs], S, None, V, *outs[k], stream=streams[k])
+
+    for i in range(4):
+        slot(i)
+    torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for st in streams:
+        st.wait_event(e0)
+    for i in range(steps):
+        slot(i)
+    for st in streams:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        main.wait_event(ev)
+    e1.record(main)
+    torch.cuda.synchronize()
+    for p in plans:
+        p.close()
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms_per_slot": ms, "vectors_per_s": V / (ms / 1e3), "slots": steps,
+            "note": "two plans on two streams, slot i + 1 factorised while slot i is precoded; inputs rotate over "
+                    f"{n_inputs} slot draws (working set > L2), no flush"}
+
+
 def measure_paper_points(dev, flush, steps: int) -> list:
     """The shapes of the paper's FPGA throughput table (K = M = 4, 8, 12, 16,
     16-QAM) as whole slots with 8 paths: vectors/s of vp_factorize +
@@ -761,6 +810,7 @@ def run_gpu(args):
         line["batched"] = measure_batched(dev, flush)
         line["batched_one_vector"] = measure_batched(dev, flush, symbols_per_problem=1)
         line["paper_points"] = measure_paper_points(dev, flush, min(args.steps, 50))
+        line["pipelined"] = measure_pipelined(dev, w, min(args.steps, 200))
     if ws == 1 and not args.no_serving:
         line["serving"] = measure_serving(dev, args.serving_slots, args.serving_lanes, args.serving_pool_mib,
                                           args.serving_paths)
