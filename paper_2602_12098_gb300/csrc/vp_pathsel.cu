@@ -433,9 +433,10 @@ cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
     a.ns = ns;
     size_t per = (size_t)6 * ns * sizeof(uint64_t);
     if (per < eval_order_bytes(n_max)) per = (eval_order_bytes(n_max) + 15) & ~size_t(15);
-    // long lists: a block of warps per channel; short ones: a warp per channel
+    // long lists: a block of warps per channel (2 warps up to 256 paths, 4 for
+    // 512-1024, measured best on GB300); short ones: a warp per channel
     a.gstride = (int)(per / sizeof(uint64_t));
-    const int tpc = n_max >= 128 ? 64 : 32;
+    const int tpc = n_max >= 512 ? 128 : (n_max >= 128 ? 64 : 32);
     int cpb = 1;
     if (tpc == 32) {
         cpb = (int)((48 * 1024) / per);
