@@ -361,6 +361,13 @@ def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
         out["graph_ms"] = ms
         out["graph_vectors_per_s"] = V / (ms / 1e3)
         del graph
+        # the project's autotuner (vp_batch_autotune): per-group mapping knobs, same outputs
+        out["tuned_knobs"] = b.autotune(reps=3, cache="", stream=stream)
+        for _ in range(3):
+            b.launch(stream)
+        ms = timed(lambda: b.launch(stream), 10)
+        out["tuned_ms"] = ms
+        out["tuned_vectors_per_s"] = V / (ms / 1e3)
 
     plans = {}
     for i in range(len(probs)):

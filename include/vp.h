@@ -298,6 +298,38 @@ vp_status vp_batch_launch(vp_batch* batch, void* stream);
 /* Kernel launches enqueued by one vp_batch_launch. */
 int vp_batch_launch_count(const vp_batch* batch);
 
+/*
+ * Autotuner. Every path-selection and search launch of a batch (a "group")
+ * has one mapping knob: the threads that work on one channel's path lists
+ * (32, 64, 128 or 256) and the warps per block of the search (1..7, i.e. the
+ * data vectors of a problem in flight at once); 0 is the built-in choice.
+ * The knobs change how the work maps to lanes, never the arithmetic: the
+ * outputs are the same for every setting.
+ *
+ * vp_batch_autotune runs the bound batch once, then times each group alone
+ * under every candidate (reps launches each, CUDA events on `stream`) and
+ * keeps the fastest. It synchronises the host with the stream (not for use
+ * inside a stream capture) and leaves the outputs of a full launch behind.
+ * Returns VP_ERR_NOT_FACTORIZED if the batch is not bound, VP_ERR_INVALID_ARG
+ * for reps outside 1..100.
+ */
+vp_status vp_batch_autotune(vp_batch* batch, int reps, void* stream);
+
+/* The knob of each group (launch order): writes min(count, max_knobs) values
+ * to the HOST array `knobs` (may be NULL) and returns count (-1 for NULL). */
+int vp_batch_get_tuning(const vp_batch* batch, int* knobs, int max_knobs);
+
+/* Set every group's knob (e.g. from a cache of earlier vp_batch_autotune
+ * results); n_knobs must equal the group count and each value must be one
+ * of the candidates above or 0, else VP_ERR_INVALID_ARG and nothing changes. */
+vp_status vp_batch_set_tuning(vp_batch* batch, const int* knobs, int n_knobs);
+
+/* Shape of each group, for keying a tuning cache: 6 ints per group in the
+ * HOST array `info` (stage 0 factor / 1 paths / 2 search, problem count,
+ * K (factor) or K tile (search) else 0, M (factor) else 0, largest n_paths,
+ * largest S); returns the group count (-1 for NULL). */
+int vp_batch_group_info(const vp_batch* batch, int* info, int max_groups);
+
 /* Free the batch (host memory only; the workspace stays the caller's). */
 vp_status vp_batch_destroy(vp_batch* batch);
 

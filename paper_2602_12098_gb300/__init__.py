@@ -29,6 +29,7 @@ __all__ = [
     "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
     "vp_job_desc", "vp_job_done", "vp_server_stats", "vp_server_create", "vp_server_submit", "vp_server_poll",
     "vp_server_drain", "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "Server",
+    "vp_batch_autotune", "vp_batch_get_tuning", "vp_batch_set_tuning", "vp_batch_group_info",
     "EXPORTED_SYMBOLS", "Plan",
 ]
 
@@ -51,7 +52,8 @@ EXPORTED_SYMBOLS = (
     "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_batch_create", "vp_batch_workspace_bytes",
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
-    "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy",
+    "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "vp_batch_autotune", "vp_batch_get_tuning",
+    "vp_batch_set_tuning", "vp_batch_group_info",
 )
 
 
@@ -150,6 +152,15 @@ def load():
             for name in ("vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
                          "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
+            L.vp_batch_autotune.argtypes = [vpp, ctypes.c_int, vpp]
+            L.vp_batch_autotune.restype = ctypes.c_int
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.vp_batch_get_tuning.argtypes = [vpp, ip, ctypes.c_int]
+            L.vp_batch_get_tuning.restype = ctypes.c_int
+            L.vp_batch_set_tuning.argtypes = [vpp, ip, ctypes.c_int]
+            L.vp_batch_set_tuning.restype = ctypes.c_int
+            L.vp_batch_group_info.argtypes = [vpp, ip, ctypes.c_int]
+            L.vp_batch_group_info.restype = ctypes.c_int
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
             for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
@@ -346,6 +357,31 @@ class Batch:
     def launch(self, stream=None):
         vp_batch_launch(self.handle, stream)
 
+    def autotune(self, reps: int = 3, cache: str | None = None, stream=None) -> list:
+        """Tune the launch mapping (vp_batch_autotune) or take it from a JSON
+        cache keyed by device name and group shapes; cache = None uses
+        $VP_TUNE_CACHE when set. Returns the knobs in force."""
+        import json
+        import torch
+        cache = cache if cache is not None else os.environ.get("VP_TUNE_CACHE")
+        key = tuning_key(self.handle, torch.cuda.get_device_name())
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                vp_batch_set_tuning(self.handle, table[key])
+                return table[key]
+        vp_batch_autotune(self.handle, reps, stream)
+        knobs = vp_batch_get_tuning(self.handle)
+        if cache:
+            table[key] = knobs
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1)
+            os.replace(tmp, cache)
+        return knobs
+
     def close(self):
         if self.handle:
             vp_batch_destroy(self.handle)
@@ -362,6 +398,42 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def vp_batch_autotune(batch: int, reps: int = 3, stream=None) -> None:
+    _check(load().vp_batch_autotune(batch, int(reps), _stream(stream)), "vp_batch_autotune")
+
+
+def vp_batch_get_tuning(batch: int) -> list:
+    n = load().vp_batch_get_tuning(batch, None, 0)
+    if n < 0:
+        raise VPError(1, "vp_batch_get_tuning")
+    buf = (ctypes.c_int * max(n, 1))()
+    load().vp_batch_get_tuning(batch, buf, n)
+    return [int(buf[i]) for i in range(n)]
+
+
+def vp_batch_set_tuning(batch: int, knobs) -> None:
+    knobs = [int(k) for k in knobs]
+    buf = (ctypes.c_int * max(len(knobs), 1))(*knobs)
+    _check(load().vp_batch_set_tuning(batch, buf, len(knobs)), "vp_batch_set_tuning")
+
+
+def vp_batch_group_info(batch: int) -> list:
+    """Per group: (stage, problems, K or K tile, M, largest n_paths, largest S)."""
+    n = load().vp_batch_group_info(batch, None, 0)
+    if n < 0:
+        raise VPError(1, "vp_batch_group_info")
+    buf = (ctypes.c_int * max(6 * n, 1))()
+    load().vp_batch_group_info(batch, buf, n)
+    return [tuple(int(buf[6 * i + k]) for k in range(6)) for i in range(n)]
+
+
+def tuning_key(batch: int, device_name: str) -> str:
+    """Cache key of a batch's tuning: the device and the groups' shapes."""
+    import hashlib
+    shape = ";".join(",".join(str(v) for v in g) for g in vp_batch_group_info(batch))
+    return device_name + "|" + hashlib.sha256(shape.encode()).hexdigest()[:16]
 
 
 def vp_server_create(pool_bytes: int, lanes: int) -> int:

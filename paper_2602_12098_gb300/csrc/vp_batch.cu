@@ -25,6 +25,7 @@ struct vp_batch {
         int stage;   // 0 factor, 1 paths, 2 search
         int start, count;
         int K, M, KT, n_max, km_max, s_max;
+        int knob = 0;   // tuned mapping: paths = threads per channel, search = warps per block (0 = default)
     };
     std::vector<vp_problem_desc> descs;
     std::vector<vp::BatchProblem> table;   // device pointers filled in by bind
@@ -264,13 +265,109 @@ vp_status vp_batch_launch(vp_batch* b, void* stream)
             return VP_ERR_CUDA;
     if (vp::launch_factor64_batch(probs, nflag, flags, N, s) != cudaSuccess) return VP_ERR_CUDA;
     for (const vp_batch::Group& g : b->groups)
-        if (g.stage == 1 && vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, s) != cudaSuccess)
+        if (g.stage == 1 && vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, s, g.knob) !=
+                                cudaSuccess)
             return VP_ERR_CUDA;
     for (const vp_batch::Group& g : b->groups)
         if (g.stage == 2 && vp::launch_search_batch(probs, ids + 2 * N + g.start, g.count, g.KT, g.km_max, g.n_max,
-                                                    g.s_max, s) != cudaSuccess)
+                                                    g.s_max, s, g.knob) != cudaSuccess)
             return VP_ERR_CUDA;
     return VP_OK;
+}
+
+// The values a group's knob may take (0 = the built-in choice).
+static bool knob_ok(int stage, int v)
+{
+    if (v == 0) return true;
+    if (stage == 1) return v == 32 || v == 64 || v == 128 || v == 256;
+    if (stage == 2) return v >= 1 && v <= 7;
+    return false;
+}
+
+vp_status vp_batch_autotune(vp_batch* b, int reps, void* stream)
+{
+    if (!b || reps < 1 || reps > 100) return VP_ERR_INVALID_ARG;
+    if (!b->ws) return VP_ERR_NOT_FACTORIZED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int N = (int)b->descs.size();
+    const vp::BatchProblem* probs = reinterpret_cast<const vp::BatchProblem*>(b->ws + b->off_table);
+    const int* ids = reinterpret_cast<const int*>(b->ws + b->off_ids);
+    // one whole launch leaves every problem's factor and paths in place: a
+    // path-selection or search group can then be rerun alone (same outputs)
+    vp_status st = vp_batch_launch(b, stream);
+    if (st != VP_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return VP_ERR_CUDA;
+    }
+    static const int kPaths[] = {32, 64, 128, 256};
+    static const int kWarps[] = {4, 5, 6, 7};
+    st = VP_OK;
+    for (vp_batch::Group& g : b->groups) {
+        if (g.stage == 0) continue;
+        const int* cand = g.stage == 1 ? kPaths : kWarps;
+        float best = INFINITY;
+        int best_v = 0;
+        for (int ci = -1; ci < 4 && st == VP_OK; ++ci) {
+            const int v = ci < 0 ? 0 : cand[ci];
+            float ms = 0.f;
+            cudaError_t e = cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                if (g.stage == 1) e = vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, s, v);
+                else e = vp::launch_search_batch(probs, ids + 2 * N + g.start, g.count, g.KT, g.km_max, g.n_max,
+                                                 g.s_max, s, v);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                st = VP_ERR_CUDA;
+                break;
+            }
+            if (ms < best) { best = ms; best_v = v; }
+        }
+        g.knob = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+int vp_batch_get_tuning(const vp_batch* b, int* knobs, int max_knobs)
+{
+    if (!b) return -1;
+    const int n = (int)b->groups.size();
+    for (int i = 0; i < n && i < max_knobs && knobs; ++i) knobs[i] = b->groups[i].knob;
+    return n;
+}
+
+vp_status vp_batch_set_tuning(vp_batch* b, const int* knobs, int n_knobs)
+{
+    if (!b || !knobs || n_knobs != (int)b->groups.size()) return VP_ERR_INVALID_ARG;
+    for (int i = 0; i < n_knobs; ++i)
+        if (!knob_ok(b->groups[i].stage, knobs[i])) return VP_ERR_INVALID_ARG;
+    for (int i = 0; i < n_knobs; ++i) b->groups[i].knob = knobs[i];
+    return VP_OK;
+}
+
+int vp_batch_group_info(const vp_batch* b, int* info, int max_groups)
+{
+    if (!b) return -1;
+    const int n = (int)b->groups.size();
+    for (int i = 0; i < n && i < max_groups && info; ++i) {
+        const vp_batch::Group& g = b->groups[i];
+        int* o = info + 6 * i;
+        o[0] = g.stage;
+        o[1] = g.count;
+        o[2] = g.stage == 0 ? g.K : (g.stage == 2 ? g.KT : 0);
+        o[3] = g.stage == 0 ? g.M : 0;
+        o[4] = g.n_max;
+        o[5] = g.s_max;
+    }
+    return n;
 }
 
 int vp_batch_launch_count(const vp_batch* b) { return b ? (int)b->groups.size() + 1 : 0; }

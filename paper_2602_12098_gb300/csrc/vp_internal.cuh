@@ -208,11 +208,14 @@ cudaError_t launch_factor32_batch(const BatchProblem* probs, const int* ids, int
 cudaError_t launch_factor64_batch(const BatchProblem* probs, const int* nflag, const int* flags, int max_flagged,
                                   cudaStream_t s);
 // pathsel: every listed problem has n_paths <= n_max.
-cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int count, int n_max, cudaStream_t s);
+// tpc: threads per channel (32, 64, 128 or 256; 0 = chosen by the list length)
+cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int count, int n_max, cudaStream_t s,
+                                 int tpc = 0);
 // search: every listed problem has K <= KT (KT in {2, 4, 8, 12, 16}) and the
 // given maxima of K*M, n_paths and S.
+// nw: warps per block (1..7; 0 = chosen from s_max)
 cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int count, int KT, int km_max,
-                                int n_max, int s_max, cudaStream_t s);
+                                int n_max, int s_max, cudaStream_t s, int nw = 0);
 
 // ---------------------------------------------------------------------------
 // Small device helpers shared by the kernels of this library.

@@ -427,7 +427,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
     eval_order(cs, out, base, n, K, nch, t, tpc);
 }
 
-cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
+cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s, int tpc_set = 0)
 {
     const int ns = n_max + (n_max >> 3);
     a.ns = ns;
@@ -436,7 +436,8 @@ cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s)
     // long lists: a block of warps per channel (2 warps up to 256 paths, 4 for
     // 512-1024, measured best on GB300); short ones: a warp per channel
     a.gstride = (int)(per / sizeof(uint64_t));
-    const int tpc = n_max >= 512 ? 128 : (n_max >= 128 ? 64 : 32);
+    int tpc = n_max >= 512 ? 128 : (n_max >= 128 ? 64 : 32);
+    if (tpc_set == 32 || tpc_set == 64 || tpc_set == 128 || tpc_set == 256) tpc = tpc_set;
     int cpb = 1;
     if (tpc == 32) {
         cpb = (int)((48 * 1024) / per);
@@ -469,13 +470,14 @@ cudaError_t launch_pathsel(const vp_plan* p, int C, cudaStream_t s)
     return run_pathsel(a, p->n_paths, s);
 }
 
-cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int count, int n_max, cudaStream_t s)
+cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int count, int n_max, cudaStream_t s,
+                                 int tpc)
 {
     PathArgs a = PathArgs();
     a.C = count;
     a.probs = probs;
     a.ids = ids;
-    return run_pathsel(a, n_max, s);
+    return run_pathsel(a, n_max, s, tpc);
 }
 
 }  // namespace vp

@@ -879,7 +879,7 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
 }
 
 cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int count, int KT, int km_max,
-                                int n_max, int s_max, cudaStream_t s)
+                                int n_max, int s_max, cudaStream_t s, int nw_set)
 {
     SearchArgs a = SearchArgs();
     a.probs = probs;
@@ -890,6 +890,7 @@ cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int c
     int nw = 7;
     if (s_max <= 7) nw = s_max < 1 ? 1 : s_max;
     else if (s_max % 7 != 0 && s_max % 6 == 0) nw = 6;
+    if (nw_set >= 1 && nw_set <= 7) nw = nw_set;
     const int threads = nw * 32;
     switch (KT) {
     case 2: return launch_kt<2>(a, count, threads, s);

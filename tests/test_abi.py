@@ -173,3 +173,31 @@ def test_server_argument_validation():
     assert lib.vp_server_reset_clock(None) == 1
     assert lib.vp_server_get_stats(None, None) == 1
     assert lib.vp_server_destroy(None) == 0
+
+
+def test_batch_tuning_knobs_host_side():
+    """Tuning knobs per launch group: group shapes, validation of set values,
+    and the autotuner's refusal on an unbound batch (all before any CUDA call)."""
+    good = [_desc(4, 8, 16, 16), _desc(8, 16, 64, 64), _desc(16, 16, 256, 1024)]
+    b = vp.vp_batch_create(good)
+    try:
+        info = vp.vp_batch_group_info(b)
+        stages = [g[0] for g in info]
+        assert stages == sorted(stages) and set(stages) == {0, 1, 2}
+        assert len(info) == vp.vp_batch_launch_count(b) - 1
+        assert vp.vp_batch_get_tuning(b) == [0] * len(info)
+        knobs = [0 if st == 0 else (128 if st == 1 else 5) for st in stages]
+        vp.vp_batch_set_tuning(b, knobs)
+        assert vp.vp_batch_get_tuning(b) == knobs
+        for bad in (knobs[:-1], [0 if st == 0 else (48 if st == 1 else 5) for st in stages],
+                    [0 if st == 0 else (64 if st == 1 else 8) for st in stages],
+                    [7 if st == 0 else 0 for st in stages]):
+            with pytest.raises(vp.VPError) as e:
+                vp.vp_batch_set_tuning(b, bad)
+            assert e.value.code == 1
+        assert vp.vp_batch_get_tuning(b) == knobs           # unchanged by the refused calls
+        with pytest.raises(vp.VPError) as e:
+            vp.vp_batch_autotune(b, 3, stream=0)
+        assert e.value.code == 5
+    finally:
+        vp.vp_batch_destroy(b)

@@ -189,3 +189,34 @@ def test_graph_replay_on_new_inputs_equals_direct_launch():
         pkd.fetch()
     assert np.array_equal(replay[0], pkd.x_np) and np.array_equal(replay[1], pkd.l_np)
     assert np.array_equal(replay[2], pkd.g_np)
+
+
+def test_autotuned_launch_equals_default_and_cache_roundtrip(tmp_path):
+    """The tuned mapping changes no output; a second batch of the same shape
+    takes its knobs from the JSON cache."""
+    probs = mixed_problems(60, 5)
+    a, t = Packed(probs), Packed(probs)
+    with vp.Batch(a.descs) as b:
+        b.launch()
+        a.fetch()
+    cache = str(tmp_path / "tune.json")
+    with vp.Batch(t.descs) as b:
+        knobs = b.autotune(reps=2, cache=cache)
+        assert len(knobs) == vp.vp_batch_launch_count(b.handle) - 1
+        b.launch()
+        t.fetch()
+    assert np.array_equal(a.x_np, t.x_np) and np.array_equal(a.l_np, t.l_np)
+    assert np.array_equal(a.g_np, t.g_np) and np.array_equal(a.st_np, t.st_np)
+    import json
+    table = json.load(open(cache))
+    assert list(table.values()) == [knobs]
+    c = Packed(probs)
+    with vp.Batch(c.descs) as b:
+        assert b.autotune(reps=2, cache=cache) == knobs
+        assert vp.vp_batch_get_tuning(b.handle) == knobs
+        # every explicit setting gives the same outputs too
+        stages = [g[0] for g in vp.vp_batch_group_info(b.handle)]
+        vp.vp_batch_set_tuning(b.handle, [0 if s == 0 else (256 if s == 1 else 3) for s in stages])
+        b.launch()
+        c.fetch()
+    assert np.array_equal(a.x_np, c.x_np) and np.array_equal(a.l_np, c.l_np) and np.array_equal(a.g_np, c.g_np)
