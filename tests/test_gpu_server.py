@@ -148,3 +148,30 @@ def test_job_larger_than_the_pool_is_refused():
             srv.submit(jd.desc())
         assert e.value.code == 6
         assert srv.stats()["submitted"] == 0
+
+
+def test_drain_deadline_returns_timeout_then_completes():
+    """vp_server_drain with a deadline shorter than the work returns
+    VP_ERR_TIMEOUT (the jobs keep running); a longer one then completes."""
+    dev = torch.device("cuda:0")
+    jobs = [JobData(400 + i, SHAPES[2], dev) for i in range(6)]
+    side = torch.cuda.Stream(device=dev)
+    ev = torch.cuda.Event()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(50_000_000)              # holds the first job's inputs for ~25 ms
+        ev.record(side)
+    with vp.Server(256 << 20, lanes=2) as srv:
+        srv.submit(jobs[0].desc(ready_event=ev))
+        for jd in jobs[1:]:
+            srv.submit(jd.desc())
+        with pytest.raises(vp.VPError) as e:
+            srv.drain(0.0)
+        assert e.value.code == 4
+        srv.drain(60.0)
+        done = srv.poll()
+        assert len(done) == len(jobs) and all(rec[1] == 0 for rec in done)
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["in_flight"] == 0 and st["queued"] == 0
+    for jd in jobs[:2]:
+        for a, b in zip(jd.outputs(), jd.alone()):
+            assert np.array_equal(a, b)
