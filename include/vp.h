@@ -60,7 +60,7 @@ typedef enum {
     VP_ERR_OOM = 3,            /* device allocation failed */
     VP_ERR_TIMEOUT = 4,        /* a bounded device wait gave up */
     VP_ERR_NOT_FACTORIZED = 5, /* vp_precode before vp_factorize, or for more channels */
-    VP_ERR_CAPACITY = 6        /* the request exceeds the fixed storage of vp_precode_noalloc */
+    VP_ERR_CAPACITY = 6        /* the request exceeds fixed storage: vp_precode_noalloc's array or a server pool */
 } vp_status;
 
 /* Per-channel status bits (the `status` output of vp_factorize). */
@@ -418,6 +418,16 @@ typedef struct {
  * pool cannot be allocated.
  */
 vp_status vp_server_create(size_t pool_bytes, int lanes, vp_server** out);
+
+/*
+ * A server with the same admission, pool accounting and reporting, whose
+ * jobs run on a host clock instead of the GPU: nothing is allocated on or
+ * sent to a device, and a job occupies its lane and pool piece for C
+ * microseconds (its channel count) from admission; job times are host
+ * milliseconds since vp_server_reset_clock. For testing and studying the
+ * scheduling without a GPU. Arguments as vp_server_create.
+ */
+vp_status vp_server_create_fake(size_t pool_bytes, int lanes, vp_server** out);
 
 /*
  * Queue a job (the descriptor is copied; the device buffers it points to

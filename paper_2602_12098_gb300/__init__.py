@@ -30,7 +30,7 @@ __all__ = [
     "vp_job_desc", "vp_job_done", "vp_server_stats", "vp_server_create", "vp_server_submit", "vp_server_poll",
     "vp_server_drain", "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "Server",
     "vp_batch_autotune", "vp_batch_get_tuning", "vp_batch_set_tuning", "vp_batch_group_info",
-    "EXPORTED_SYMBOLS", "Plan",
+    "vp_server_create_fake", "EXPORTED_SYMBOLS", "Plan",
 ]
 
 VP_CH_NONFINITE = 1
@@ -53,7 +53,7 @@ EXPORTED_SYMBOLS = (
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
     "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "vp_batch_autotune", "vp_batch_get_tuning",
-    "vp_batch_set_tuning", "vp_batch_group_info",
+    "vp_batch_set_tuning", "vp_batch_group_info", "vp_server_create_fake",
 )
 
 
@@ -143,6 +143,8 @@ def load():
             L.vp_precode_batch_workspace_bytes.restype = ctypes.c_size_t
             sp = ctypes.c_void_p
             L.vp_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(sp)]
+            L.vp_server_create_fake.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(sp)]
+            L.vp_server_create_fake.restype = ctypes.c_int
             L.vp_server_submit.argtypes = [sp, ctypes.POINTER(vp_job_desc), ctypes.POINTER(ctypes.c_int64)]
             L.vp_server_poll.argtypes = [sp, ctypes.POINTER(vp_job_done), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
             L.vp_server_drain.argtypes = [sp, ctypes.c_double]
@@ -442,6 +444,12 @@ def vp_server_create(pool_bytes: int, lanes: int) -> int:
     return h.value
 
 
+def vp_server_create_fake(pool_bytes: int, lanes: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().vp_server_create_fake(int(pool_bytes), int(lanes), ctypes.byref(h)), "vp_server_create_fake")
+    return h.value
+
+
 def vp_server_submit(server: int, job: vp_job_desc) -> int:
     i = ctypes.c_int64()
     _check(load().vp_server_submit(server, ctypes.byref(job), ctypes.byref(i)), "vp_server_submit")
@@ -490,8 +498,8 @@ def job_desc(K, M, qam, n_paths, C, S, H, sym, x, l, gamma, status=None, tau=0.0
 class Server:
     """Owning handle of a vp_server (destroys it on close / exit of a with-block)."""
 
-    def __init__(self, pool_bytes: int, lanes: int = 4):
-        self.handle = vp_server_create(pool_bytes, lanes)
+    def __init__(self, pool_bytes: int, lanes: int = 4, fake: bool = False):
+        self.handle = (vp_server_create_fake if fake else vp_server_create)(pool_bytes, lanes)
 
     def submit(self, job: vp_job_desc) -> int:
         return vp_server_submit(self.handle, job)

@@ -117,7 +117,7 @@ const char* vp_status_string(vp_status s)
     case VP_ERR_OOM: return "out of device memory";
     case VP_ERR_TIMEOUT: return "device wait timed out";
     case VP_ERR_NOT_FACTORIZED: return "no factorised channels";
-    case VP_ERR_CAPACITY: return "exceeds the fixed storage of vp_precode_noalloc";
+    case VP_ERR_CAPACITY: return "exceeds the fixed storage (vp_precode_noalloc array or server pool)";
     }
     return "unknown status";
 }

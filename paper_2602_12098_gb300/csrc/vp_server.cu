@@ -3,6 +3,11 @@
 // state carved from one device pool. Admission is first come, first served,
 // gated by an idle lane and a first-fit piece of the pool; progress (retiring
 // finished jobs, admitting waiting ones) happens inside the calls.
+//
+// A server made by vp_server_create_fake runs the same admission, pool and
+// reporting logic on a host clock instead of the GPU (a job "runs" for its
+// channel count in microseconds), so that the scheduling can be tested, and
+// studied, without a device.
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -74,6 +79,7 @@ struct Job {
     int lane = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int status = VP_OK;
+    double fake_t0 = 0.0, fake_t1 = 0.0;   // host-clock run of a fake server's job (ms)
 };
 
 bool finite_nonneg(float v) { return v >= 0.f && std::isfinite(v); }
@@ -115,6 +121,9 @@ vp_plan plan_of(const vp_job_desc& j)
 
 struct vp_server {
     std::mutex mu;
+    bool fake = false;                    // host-clock executor, no device work
+    int nlanes = 0;
+    std::chrono::steady_clock::time_point t_ref;
     int device = 0;
     size_t pool_bytes = 0;
     unsigned char* pool_base = nullptr;
@@ -132,6 +141,11 @@ struct vp_server {
 };
 
 namespace {
+
+double host_ms(const vp_server* s)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s->t_ref).count();
+}
 
 cudaError_t take_event(vp_server* s, cudaEvent_t* e)
 {
@@ -162,6 +176,16 @@ void retire(vp_server* s)
     for (size_t i = 0; i < s->running.size();) {
         const int64_t id = s->running[i];
         Job& j = s->jobs[id];
+        if (s->fake) {
+            if (host_ms(s) < j.fake_t1) {
+                ++i;
+                continue;
+            }
+            finish(s, id, j, (float)j.fake_t0, (float)j.fake_t1);
+            s->running[i] = s->running.back();
+            s->running.pop_back();
+            continue;
+        }
         const cudaError_t q = cudaEventQuery(j.ev1);
         if (q == cudaErrorNotReady) {
             ++i;
@@ -184,7 +208,7 @@ void admit(vp_server* s)
 {
     while (!s->waiting.empty()) {
         int lane = -1;
-        for (int k = 0; k < (int)s->lanes.size(); ++k)
+        for (int k = 0; k < s->nlanes; ++k)
             if (s->lane_job[k] == 0) { lane = k; break; }
         if (lane < 0) return;
         const int64_t id = s->waiting.front();
@@ -195,6 +219,13 @@ void admit(vp_server* s)
         j.off = off;
         j.lane = lane;
         s->lane_job[lane] = id;
+        if (s->fake) {
+            j.fake_t0 = host_ms(s);
+            j.fake_t1 = j.fake_t0 + 1e-3 * j.desc.C;
+            s->running.push_back(id);
+            if ((int)s->running.size() > s->max_in_flight) s->max_in_flight = (int)s->running.size();
+            continue;
+        }
         vp::carve_state(s->pool_base + off, j.desc.C, j.plan.K, vp::p_rows(&j.plan), j.plan.n_paths, &j.plan.d);
         j.plan.cap = j.desc.C;
         j.plan.cap_mp = vp::p_rows(&j.plan);
@@ -258,6 +289,7 @@ vp_status vp_server_create(size_t pool_bytes, int lanes, vp_server** out)
         ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
         if (ok) s->lanes.push_back(st);
     }
+    s->nlanes = (int)s->lanes.size();
     s->lane_job.assign(s->lanes.size(), 0);
     ok = ok && cudaEventCreate(&s->ref) == cudaSuccess;
     if (!ok) {
@@ -269,6 +301,27 @@ vp_status vp_server_create(size_t pool_bytes, int lanes, vp_server** out)
         vp_server_destroy(s);
         return VP_ERR_CUDA;
     }
+    *out = s;
+    return VP_OK;
+}
+
+vp_status vp_server_create_fake(size_t pool_bytes, int lanes, vp_server** out)
+{
+    if (!out) return VP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (pool_bytes < (size_t(1) << 20) || lanes < 1 || lanes > kMaxLanes) return VP_ERR_INVALID_ARG;
+    vp_server* s = new (std::nothrow) vp_server();
+    if (!s) return VP_ERR_OOM;
+    s->pool = new (std::nothrow) Pool(pool_bytes);
+    if (!s->pool) {
+        delete s;
+        return VP_ERR_OOM;
+    }
+    s->fake = true;
+    s->pool_bytes = pool_bytes;
+    s->nlanes = lanes;
+    s->lane_job.assign((size_t)lanes, 0);
+    s->t_ref = std::chrono::steady_clock::now();
     *out = s;
     return VP_OK;
 }
@@ -323,8 +376,12 @@ vp_status vp_server_drain(vp_server* s, double timeout_s)
 
 vp_status vp_server_reset_clock(vp_server* s)
 {
-    if (!s || s->lanes.empty()) return VP_ERR_INVALID_ARG;
+    if (!s || s->nlanes < 1) return VP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(s->mu);
+    if (s->fake) {
+        s->t_ref = std::chrono::steady_clock::now();
+        return VP_OK;
+    }
     if (cudaEventRecord(s->ref, s->lanes[0]) != cudaSuccess || cudaEventSynchronize(s->ref) != cudaSuccess) {
         cudaGetLastError();
         return VP_ERR_CUDA;
@@ -336,7 +393,7 @@ vp_status vp_server_get_stats(vp_server* s, vp_server_stats* out)
 {
     if (!s || !out) return VP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(s->mu);
-    out->lanes = (int)s->lanes.size();
+    out->lanes = s->nlanes;
     out->queued = (int)s->waiting.size();
     out->in_flight = (int)s->running.size();
     out->max_in_flight = s->max_in_flight;
@@ -351,6 +408,11 @@ vp_status vp_server_get_stats(vp_server* s, vp_server_stats* out)
 vp_status vp_server_destroy(vp_server* s)
 {
     if (!s) return VP_OK;
+    if (s->fake) {
+        delete s->pool;
+        delete s;
+        return VP_OK;
+    }
     for (cudaStream_t st : s->lanes) cudaStreamSynchronize(st);
     for (auto& kv : s->jobs) {
         if (kv.second.ev0) cudaEventDestroy(kv.second.ev0);

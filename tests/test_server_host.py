@@ -1,0 +1,112 @@
+"""The job server's scheduling on the host (vp_server_create_fake: the same
+admission, pool accounting and reporting as the GPU server, jobs running on
+a host clock for C microseconds). No GPU: these cover first-come admission
+by idle lane and pool space, head-of-line waiting, the pool's bookkeeping,
+the drain deadline, and reporting each job once.
+"""
+import time
+
+import pytest
+
+import paper_2602_12098_gb300 as vp
+
+K, M, N_PATHS = 16, 16, 256
+
+
+def per_channel_bytes():
+    # the state layout of one channel (the library rounds each piece to 256 B)
+    return 24 * K * K + 16 * K * M + 20 * N_PATHS + 5 * K + 300
+
+
+def job(C, S=14):
+    # pointers are never dereferenced by the fake executor; they must be non-null
+    return vp.job_desc(K, M, 256, N_PATHS, C, S, 16, 16, 16, 16, 16)
+
+
+def drain_all(srv, timeout=20.0):
+    srv.drain(timeout)
+    return srv.poll()
+
+
+def test_jobs_complete_and_are_reported_once():
+    with vp.Server(64 << 20, lanes=3, fake=True) as srv:
+        ids = [srv.submit(job(C)) for C in (200, 300, 100, 50, 400, 80)]
+        done = drain_all(srv)
+        assert sorted(r[0] for r in done) == sorted(ids)
+        assert all(r[1] == 0 and 0.0 <= r[2] <= r[3] for r in done)
+        assert srv.poll() == []
+        st = srv.stats()
+        assert st["completed"] == st["submitted"] == 6 and st["queued"] == 0 and st["in_flight"] == 0
+        assert st["pool_used"] == 0 and 1 < st["max_in_flight"] <= 3
+
+
+def test_simulated_run_time_and_lanes():
+    """Each job holds a lane for C microseconds: four 20 ms jobs on two lanes
+    take two rounds."""
+    with vp.Server(4 << 30, lanes=2, fake=True) as srv:      # host bookkeeping only: nothing allocated
+        srv.reset_clock()
+        for _ in range(4):
+            srv.submit(job(20000))
+        done = sorted(drain_all(srv), key=lambda r: r[0])
+        for r in done:
+            assert r[3] - r[2] == pytest.approx(20.0, abs=0.5)
+        # the third and fourth start when the first two end
+        assert done[2][2] >= done[0][3] - 0.5 and done[3][2] >= done[1][3] - 0.5
+        assert srv.stats()["max_in_flight"] == 2
+
+
+def test_admission_waits_for_pool_space_first_come():
+    """A job that does not fit waits at the head of the queue and the jobs
+    behind it wait too (first come, first served), until space frees up."""
+    unit = per_channel_bytes()
+    pool = 1000 * unit + (1 << 20)
+    with vp.Server(pool, lanes=4, fake=True) as srv:
+        srv.reset_clock()
+        a = srv.submit(job(600))        # 600 us, 600 channels of state
+        b = srv.submit(job(700))        # does not fit beside a: waits
+        c = srv.submit(job(10))         # would fit, but queues behind b
+        st = srv.stats()
+        assert st["in_flight"] == 1 and st["queued"] == 2
+        done = {r[0]: r for r in drain_all(srv)}
+        assert done[b][2] >= done[a][3] - 0.2          # b admitted after a ended
+        assert done[c][2] >= done[b][2] - 0.2          # c not before b
+        assert srv.stats()["pool_high_water"] <= pool
+
+
+def test_pool_accounting_coalesces():
+    unit = per_channel_bytes()
+    with vp.Server(100 * unit + (1 << 20), lanes=8, fake=True) as srv:
+        for _ in range(4):
+            srv.submit(job(25))
+        st = srv.stats()
+        assert st["in_flight"] == 4 and st["pool_used"] >= 4 * 25 * unit
+        drain_all(srv)
+        # freed pieces merge back: a job of nearly the whole pool fits again
+        srv.submit(job(100))
+        assert srv.stats()["in_flight"] == 1
+        drain_all(srv)
+        assert srv.stats()["pool_used"] == 0
+
+
+def test_drain_deadline_and_refusals():
+    with vp.Server(1 << 30, lanes=1, fake=True) as srv:
+        with pytest.raises(vp.VPError) as e:         # larger than the whole pool
+            srv.submit(job(100000))
+        assert e.value.code == 6
+        with pytest.raises(vp.VPError) as e:         # out-of-range descriptor
+            srv.submit(vp.job_desc(17, 16, 256, 256, 10, 14, 16, 16, 16, 16, 16))
+        assert e.value.code == 1
+        srv.submit(job(30000))                      # 30 ms
+        t0 = time.perf_counter()
+        with pytest.raises(vp.VPError) as e:
+            srv.drain(0.005)
+        assert e.value.code == 4 and time.perf_counter() - t0 < 1.0
+        drain_all(srv)
+        assert srv.stats()["completed"] == 1
+
+
+def test_destroy_with_waiting_jobs():
+    srv = vp.Server(2 << 20, lanes=1, fake=True)
+    for _ in range(3):
+        srv.submit(job(10))
+    srv.close()
