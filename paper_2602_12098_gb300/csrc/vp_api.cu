@@ -1,7 +1,10 @@
 // C-ABI of libvp: plan lifecycle, argument checks and kernel sequencing.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "vp_internal.cuh"
 
@@ -105,6 +108,26 @@ void* mapped(const void* hp)
 }
 
 }  // namespace
+
+namespace vp {
+
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> raised;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = raised[std::make_pair(kernel, dev)];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
+}  // namespace vp
 
 extern "C" {
 

@@ -692,12 +692,8 @@ cudaError_t run_factor64(const FactorArgs& a, int max_flagged, cudaStream_t s)
     if (blocks > 152 * 2) blocks = 152 * 2;
     if (blocks < 1) blocks = 1;
     const size_t sh = 4 * sizeof(Smem64);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(factor64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(factor64_kernel), sh);
+    if (e != cudaSuccess) return e;
     factor64_kernel<<<blocks, 128, sh, s>>>(a);
     return cudaGetLastError();
 }

@@ -190,6 +190,11 @@ size_t carve_state(unsigned char* base, int C, int K, int Mp, int n, DeviceState
 cudaError_t enqueue_slot(const vp_plan* p, const float2* H, int C, const uint8_t* sym, int S, float2* x, int8_t* l,
                          float* gamma, uint8_t* status, cudaStream_t s);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device (once per kernel, device and size; thread-safe). A no-op under the
+// default 48 KB.
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes);
+
 // Kernel launchers (each returns cudaSuccess or the launch error).
 cudaError_t launch_factor32(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
                             uint8_t* ul_out, cudaStream_t s);

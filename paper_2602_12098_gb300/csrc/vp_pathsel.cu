@@ -444,13 +444,8 @@ cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s, int tpc_set = 0)
         cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
     }
     const size_t shbytes = per * cpb;
-    static size_t attr_set = 0;
-    if (shbytes > 40 * 1024 && shbytes > attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pathsel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)shbytes);
-        if (e != cudaSuccess) return e;
-        attr_set = shbytes;
-    }
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(pathsel_kernel), shbytes);
+    if (e != cudaSuccess) return e;
     pathsel_kernel<<<(a.C + cpb - 1) / cpb, tpc * cpb, shbytes, s>>>(a, cpb);
     return cudaGetLastError();
 }

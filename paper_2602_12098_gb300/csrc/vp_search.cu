@@ -779,13 +779,8 @@ cudaError_t launch_small(const SearchArgs& a, int C, int per, cudaStream_t s)
     int nw = (per + G - 1) / G;
     nw = nw < 1 ? 1 : (nw > 7 ? 7 : nw);
     const size_t sh = (size_t)small_smem(KT, a.K * a.Mp, nw, G).total;
-    static size_t attr = 0;
-    if (sh > 40 * 1024 && sh > attr) {
-        cudaError_t e = cudaFuncSetAttribute(search_small_kernel<KT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sh);
-        if (e != cudaSuccess) return e;
-        attr = sh;
-    }
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_small_kernel<KT, G>), sh);
+    if (e != cudaSuccess) return e;
     search_small_kernel<KT, G><<<C, nw * 32, sh, s>>>(a);
     return cudaGetLastError();
 }
@@ -801,13 +796,8 @@ cudaError_t launch_small_kt(const SearchArgs& a, int C, int per, cudaStream_t s)
 template <int KT, bool BATCH, bool LUT, bool FIX>
 cudaError_t launch_one(const SearchArgs& a, int C, int threads, size_t sh, cudaStream_t s)
 {
-    static size_t attr = 0;
-    if (sh > 40 * 1024 && sh > attr) {
-        cudaError_t e = cudaFuncSetAttribute(search_kernel<KT, BATCH, LUT, FIX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e != cudaSuccess) return e;
-        attr = sh;
-    }
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_kernel<KT, BATCH, LUT, FIX>), sh);
+    if (e != cudaSuccess) return e;
     search_kernel<KT, BATCH, LUT, FIX><<<C, threads, sh, s>>>(a);
     return cudaGetLastError();
 }
