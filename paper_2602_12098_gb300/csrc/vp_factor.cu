@@ -9,10 +9,8 @@
 //   matrix route squares the condition number). One half-warp per channel,
 //   lane j holds column j of A in registers.
 // factor64_kernel: channels whose estimated cond(H H^H) (power iteration on R
-//   and U) passes the plan threshold are redone with FP64 (one warp per
-//   channel, or four when at most one flagged channel falls to each block):
-//   the Gram matrix (compensated FP32 sums, exact for FP32 input), pivoted
-//   reverse Cholesky
+//   and U) passes the plan threshold are redone with FP64: the Gram matrix
+//   (compensated FP32 sums, exact for FP32 input), pivoted reverse Cholesky
 //   with the same min-pivot rule, U = R^-1 and one Newton step
 //   U <- U (2I - R U) in FP64, then P = H^H U^H U as a hi/lo FP32 pair.
 //
@@ -352,13 +350,14 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 }
 
 // ---------------------------------------------------------------------------
-// FP64 path for the flagged channels: one warp per channel (four warps when
-// few are flagged), threads strided over the entries of each (triangular)
-// matrix operation. GB300 issues FP64 FMAs
+// FP64 path for the flagged channels: one warp per channel, lanes strided over
+// the entries of each (triangular) matrix operation. GB300 issues FP64 FMAs
 // at 1/64 of the FP32 rate, so FP64 is kept to the pivoted Cholesky of the
 // Gram matrix, U = R^-1 and one Newton step, with the lanes of every FP64
 // instruction packed; the Gram matrix, A = U2^H U2 and P = H^H A are
 // accumulated in compensated FP32 (exact products, ~48-bit sums).
+
+constexpr int kW64 = 1;   // channels (warps) per block (27 KB of shared memory each)
 
 struct Smem64 {
     float2 h[kMaxK][kMaxM];      // H rows (user order)
@@ -398,256 +397,233 @@ __device__ __forceinline__ void cdot2(float2 x, float2 yh, float2 yl, float& re,
     ime = fmaf(x.x, yl.y, fmaf(x.y, yl.x, ime));
 }
 
-// Barrier of the threads working on one channel: the warp, or the block.
-template <int NT>
-__device__ __forceinline__ void gsync()
+__global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
 {
-    if (NT == 32) __syncwarp();
-    else __syncthreads();
-}
-
-// The FP64 fix-up of channel c by NT threads (a warp, or a block of 4 warps
-// when few channels are flagged: the same steps with 4x the lanes on the
-// entry loops, which shortens the per-channel chain). The small reductions
-// (largest diagonal, pivot) run on lanes 0-31 of every warp over the same
-// shared values, so every thread holds their results.
-template <int NT>
-__device__ void fp64_channel(const FactorArgs& a, Smem64& sm, int c, int tid)
-{
-    const int lane = tid & 31;
-    const int K = a.probs ? a.probs[c].K : a.K;
-    const int M = a.probs ? a.probs[c].M : a.M;
-    const int Mp = a.probs ? M : a.Mp;
-    const float lam = a.probs ? 0.f : a.lambda;
-    const FChan f = fchan(a, c, K, M);
-    for (int i = tid; i < K * M; i += NT) sm.h[i / M][i % M] = f.H[i];
-    if (tid < K) sm.rem[tid] = tid;
-    gsync<NT>();
-    // Gram matrix (compensated FP32, exact for FP32 input), both triangles in FP64
-    for (int e = tid; e < K * (K + 1) / 2; e += NT) {
-        int r, q;
-        tri_index(e, r, q);
-        float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
-        for (int m = 0; m < M; ++m) {
-            const float2 x = sm.h[r][m], y = sm.h[q][m];
-            dot2_acc(x.x, y.x, re, ree);
-            dot2_acc(x.y, y.y, re, ree);
-            dot2_acc(x.y, y.x, im, ime);
-            dot2_acc(-x.x, y.y, im, ime);
-        }
-        double2 g = make_double2((double)re + (double)ree, (double)im + (double)ime);
-        if (r == q) g.x += (double)lam * (double)lam;          // H H^H + lambda^2 I
-        sm.s[r][q] = g;
-        sm.s[q][r] = zconj(g);
-    }
-    gsync<NT>();
-    // every warp reduces the same shared values, so every thread holds the result
-    double dmax = lane < K ? sm.s[lane][lane].x : 0.0;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
-
-    // pivoted reverse Cholesky (level t from K-1 down: smallest Schur diagonal, ties to the lowest user)
-    bool singular = false;
-    for (int t = K - 1; t >= 0; --t) {
-        const int m = t + 1;                                       // remaining users before the pivot
-        // smallest diagonal: the doubles compared as ordered integers (sign-folded bit
-        // patterns), which keeps the comparisons off the FP64 pipe
-        long long ik = 0x7ff0000000000000ll;                        // +infinity
-        int ku = 0x7fffffff, kp = lane;
-        if (lane < m) {
-            ku = sm.rem[lane];
-            const long long b = __double_as_longlong(sm.s[ku][ku].x);
-            ik = b ^ ((b >> 63) & 0x7fffffffffffffffll);
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const long long ok = __shfl_xor_sync(kFull, ik, o);
-            const int ou = __shfl_xor_sync(kFull, ku, o), op = __shfl_xor_sync(kFull, kp, o);
-            if (ok < ik || (ok == ik && ou < ku)) { ik = ok; ku = ou; kp = op; }
-        }
-        const double key = __longlong_as_double(ik ^ ((ik >> 63) & 0x7fffffffffffffffll));
-        if (!(key > 1e-12 * dmax)) { singular = true; break; }      // uniform across the warp
-        const int p = ku;
-        // 1 / sqrt(key): FP32 estimate, two Newton steps in FP64 (y <- y (3 - k y^2) / 2,
-        // each doubling the correct bits), then sqrt(key) = key / sqrt(key)
-        double irt = (double)rsqrtf((float)key);
-        if (!(irt > 0.0 && irt < INFINITY)) irt = 1.0 / sqrt(key);   // key outside the FP32 range
-        irt = irt * (1.5 - 0.5 * key * irt * irt);
-        irt = irt * (1.5 - 0.5 * key * irt * irt);
-        const double rt = key * irt;
-        // remove p from the remaining list (move the last one into its position)
-        const int last = sm.rem[m - 1];
-        gsync<NT>();
-        if (tid == 0) {
-            sm.rem[kp] = last;
-            sm.rd[t] = rt;
-            sm.rinv[t] = irt;
-            sm.uol[t] = p;
-        }
-        gsync<NT>();
-        if (tid < m - 1) {
-            const double2 v = sm.s[sm.rem[tid]][p];
-            const double2 l = make_double2(v.x * irt, v.y * irt);
-            sm.pc[tid] = l;
-            sm.lc[t][sm.rem[tid]] = l;
-        }
-        gsync<NT>();
-        for (int e = tid; e < (m - 1) * m / 2; e += NT) {        // Schur update, packed lower triangle
-            int ia, ib;
-            tri_index(e, ia, ib);
-            const int ua = sm.rem[ia], ub = sm.rem[ib];
-            const double2 pr = zmul(sm.pc[ia], zconj(sm.pc[ib]));
-            const double2 v = make_double2(sm.s[ua][ub].x - pr.x, sm.s[ua][ub].y - pr.y);
-            sm.s[ua][ub] = v;
-            sm.s[ub][ua] = zconj(v);
-        }
-        gsync<NT>();
-    }
-
-    if (!singular) {
-        for (int e = tid; e < K * K; e += NT) {                    // R in level order
-            const int r = e / K, q = e % K;
-            sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
-        }
-        gsync<NT>();
-        for (int e = tid; e < K * K; e += NT) sm.lc[e / K][e % K] = make_double2(0.0, 0.0);
-        gsync<NT>();
-        // U = R^-1 by rows from the bottom: U_m. = (e_m - sum_{j>m} R_mj U_j.) / R_mm
-        for (int m = K - 1; m >= 0; --m) {
-            if (tid < K) {
-                const int k = tid;
-                const double2 acc = sm.lc[m][k];
-                const double ri = sm.rinv[m];
-                sm.u[m][k] = (k < m) ? make_double2(0.0, 0.0)
-                                     : make_double2(((k == m ? 1.0 : 0.0) - acc.x) * ri, -acc.y * ri);
-            }
-            gsync<NT>();
-            const int w = K - m;                                    // entries (i < m, k >= m)
-            for (int e = tid; e < m * w; e += NT) {
-                const int i = e / w, k = m + e % w;
-                sm.lc[i][k] = zfma(sm.r[i][m], sm.u[m][k], sm.lc[i][k]);
-            }
-            gsync<NT>();
-        }
-        // one Newton step: E = I - R U, U2 = U + U E (both upper triangular), accumulated by rank-1 steps
-        for (int e = tid; e < K * K; e += NT) {
-            const int r = e / K, q = e % K;
-            sm.s[r][q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
-        }
-        gsync<NT>();
-        for (int m = 0; m < K; ++m) {                               // E_ik -= R_im U_mk, i <= m <= k
-            const int w = K - m;
-            for (int e = tid; e < (m + 1) * w; e += NT) {
-                const int i = e / w, k = m + e % w;
-                const double2 pr = zmul(sm.r[i][m], sm.u[m][k]);
-                sm.s[i][k].x -= pr.x;
-                sm.s[i][k].y -= pr.y;
-            }
-            gsync<NT>();
-        }
-        for (int e = tid; e < K * K; e += NT) sm.lc[e / K][e % K] = sm.u[e / K][e % K];
-        gsync<NT>();
-        for (int m = 0; m < K; ++m) {                               // U2_ik += U_im E_mk, i <= m <= k
-            const int w = K - m;
-            for (int e = tid; e < (m + 1) * w; e += NT) {
-                const int i = e / w, k = m + e % w;
-                sm.lc[i][k] = zfma(sm.u[i][m], sm.s[m][k], sm.lc[i][k]);
-            }
-            gsync<NT>();
-        }
-        // U2 (in lc) as FP32 hi + lo; outputs: row r of U~, w_r, user of level r
-        if (tid < K) sm.rd[tid] = 1.0 / sm.lc[tid][tid].x;         // 1 / U2_rr
-        gsync<NT>();
-        for (int e = tid; e < K * K; e += NT) {
-            const int r = e / K, q = e % K;
-            const double2 v = sm.lc[r][q];
-            const float hx = (float)v.x, hy = (float)v.y;
-            sm.uh[r][q] = make_float2(hx, hy);
-            sm.ul[r][q] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
-            const double urr = sm.lc[r][r].x, iurr = sm.rd[r];
-            const float2 ut = (q > r) ? make_float2((float)(v.x * iurr), (float)(v.y * iurr))
-                                      : (q == r ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
-            f.s.utp[r * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
-            f.s.utc[q * K + r] = ut;
-            if (f.U_out) f.U_out[r * K + q] = make_float2(hx, hy);
-            if (q == 0) {
-                f.s.w[r] = (float)(urr * urr);
-                f.s.ul[r] = (uint8_t)sm.uol[r];
-                if (f.ul_out) f.ul_out[r] = (uint8_t)sm.uol[r];
-            }
-        }
-        gsync<NT>();
-        // A = U2^H U2 (Hermitian) in compensated FP32: A_ik = sum_{m <= min(i,k)} conj(U2_mi) U2_mk
-        for (int e = tid; e < K * (K + 1) / 2; e += NT) {
-            int i, k;
-            tri_index(e, i, k);                                     // i >= k
-            float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
-            for (int m = 0; m <= k; ++m) {
-                const float2 xh = sm.uh[m][i], xl = sm.ul[m][i];
-                const float2 cx = make_float2(xh.x, -xh.y);
-                cdot2(cx, sm.uh[m][k], sm.ul[m][k], re, ree, im, ime);
-                ree = fmaf(xl.x, sm.uh[m][k].x, fmaf(xl.y, sm.uh[m][k].y, ree));    // conj(xl) * yh
-                ime = fmaf(xl.x, sm.uh[m][k].y, fmaf(-xl.y, sm.uh[m][k].x, ime));
-            }
-            const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
-            const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
-            sm.ahi[i][k] = hi;
-            sm.alo[i][k] = lo;
-            sm.ahi[k][i] = make_float2(hi.x, -hi.y);
-            sm.alo[k][i] = make_float2(lo.x, -lo.y);
-        }
-        gsync<NT>();
-        // P_level[m][k] = sum_j conj(H_perm[j][m]) A[j][k], compensated FP32
-        for (int e = tid; e < M * K; e += NT) {
-            const int m = e / K, k = e % K;
-            float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
-            for (int j = 0; j < K; ++j) {
-                const float2 hv = sm.h[sm.uol[j]][m];
-                cdot2(make_float2(hv.x, -hv.y), sm.ahi[j][k], sm.alo[j][k], re, ree, im, ime);
-            }
-            const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
-            const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
-            const int uk = sm.uol[k];
-            f.s.pt[uk * Mp + m] = hi;
-            f.s.ptlo[uk * Mp + m] = lo;
-            if (f.P_out) f.P_out[m * K + uk] = hi;
-        }
-        // regularisation rows (lambda > 0): row M + u of P is lambda A[level of u][.]
-        for (int e = tid; e < (Mp - M) * K; e += NT) {
-            const int u = e / K, k = e % K;
-            int lu = 0;
-            for (int i = 0; i < K; ++i) lu = (sm.uol[i] == u) ? i : lu;
-            const float2 ah = sm.ahi[lu][k], al = sm.alo[lu][k];
-            float hx, ex, hy, ey;
-            two_prod(lam, ah.x, hx, ex);
-            two_prod(lam, ah.y, hy, ey);
-            const int uk = sm.uol[k];
-            f.s.pt[uk * Mp + M + u] = make_float2(hx, hy);
-            f.s.ptlo[uk * Mp + M + u] = make_float2(fmaf(lam, al.x, ex), fmaf(lam, al.y, ey));
-        }
-        if (tid == 0) f.s.st[0] = (uint8_t)VP_CH_FP64;
-    } else {
-        if (tid < 16) write_channel_outputs_zero(f, K, M, Mp, tid);
-        if (tid == 0) f.s.st[0] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
-    }
-    gsync<NT>();
-}
-
-__global__ void __launch_bounds__(128) factor64_kernel(FactorArgs a)
-{
-    extern __shared__ __align__(16) unsigned char sm64raw[];
-    Smem64* smem = reinterpret_cast<Smem64*>(sm64raw);       // [4]: one per warp
+    __shared__ Smem64 smem[kW64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Smem64& sm = smem[warp];
     const int nflag = *a.nflag_in;
-    if (nflag <= (int)gridDim.x) {
-        // at most one flagged channel per block: all four warps on it
-        for (int slot = blockIdx.x; slot < nflag; slot += gridDim.x)
-            fp64_channel<128>(a, smem[0], a.flags[slot], threadIdx.x);
-        return;
+
+    for (int slot = blockIdx.x * kW64 + warp; slot < nflag; slot += gridDim.x * kW64) {
+        const int c = a.flags[slot];
+        const int K = a.probs ? a.probs[c].K : a.K;
+        const int M = a.probs ? a.probs[c].M : a.M;
+        const int Mp = a.probs ? M : a.Mp;
+        const float lam = a.probs ? 0.f : a.lambda;
+        const FChan f = fchan(a, c, K, M);
+        for (int i = lane; i < K * M; i += 32) sm.h[i / M][i % M] = f.H[i];
+        if (lane < K) sm.rem[lane] = lane;
+        __syncwarp();
+        // Gram matrix (compensated FP32, exact for FP32 input), both triangles in FP64
+        for (int e = lane; e < K * (K + 1) / 2; e += 32) {
+            int r, q;
+            tri_index(e, r, q);
+            float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
+            for (int m = 0; m < M; ++m) {
+                const float2 x = sm.h[r][m], y = sm.h[q][m];
+                dot2_acc(x.x, y.x, re, ree);
+                dot2_acc(x.y, y.y, re, ree);
+                dot2_acc(x.y, y.x, im, ime);
+                dot2_acc(-x.x, y.y, im, ime);
+            }
+            double2 g = make_double2((double)re + (double)ree, (double)im + (double)ime);
+            if (r == q) g.x += (double)lam * (double)lam;          // H H^H + lambda^2 I
+            sm.s[r][q] = g;
+            sm.s[q][r] = zconj(g);
+        }
+        __syncwarp();
+        double dmax = lane < K ? sm.s[lane][lane].x : 0.0;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+
+        // pivoted reverse Cholesky (level t from K-1 down: smallest Schur diagonal, ties to the lowest user)
+        bool singular = false;
+        for (int t = K - 1; t >= 0; --t) {
+            const int m = t + 1;                                       // remaining users before the pivot
+            // smallest diagonal: the doubles compared as ordered integers (sign-folded bit
+            // patterns), which keeps the comparisons off the FP64 pipe
+            long long ik = 0x7ff0000000000000ll;                        // +infinity
+            int ku = 0x7fffffff, kp = lane;
+            if (lane < m) {
+                ku = sm.rem[lane];
+                const long long b = __double_as_longlong(sm.s[ku][ku].x);
+                ik = b ^ ((b >> 63) & 0x7fffffffffffffffll);
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const long long ok = __shfl_xor_sync(kFull, ik, o);
+                const int ou = __shfl_xor_sync(kFull, ku, o), op = __shfl_xor_sync(kFull, kp, o);
+                if (ok < ik || (ok == ik && ou < ku)) { ik = ok; ku = ou; kp = op; }
+            }
+            const double key = __longlong_as_double(ik ^ ((ik >> 63) & 0x7fffffffffffffffll));
+            // a NaN diagonal orders above +infinity here, so with every remaining
+            // diagonal NaN the winner is an inactive lane (ku not a user): singular
+            if (ku < 0 || ku >= K || kp >= m || !(key > 1e-12 * dmax)) { singular = true; break; }   // uniform
+            const int p = ku;
+            // 1 / sqrt(key): FP32 estimate, two Newton steps in FP64 (y <- y (3 - k y^2) / 2,
+            // each doubling the correct bits), then sqrt(key) = key / sqrt(key)
+            double irt = (double)rsqrtf((float)key);
+            if (!(irt > 0.0 && irt < INFINITY)) irt = 1.0 / sqrt(key);   // key outside the FP32 range
+            irt = irt * (1.5 - 0.5 * key * irt * irt);
+            irt = irt * (1.5 - 0.5 * key * irt * irt);
+            const double rt = key * irt;
+            // remove p from the remaining list (move the last one into its position)
+            const int last = sm.rem[m - 1];
+            __syncwarp();
+            if (lane == 0) {
+                sm.rem[kp] = last;
+                sm.rd[t] = rt;
+                sm.rinv[t] = irt;
+                sm.uol[t] = p;
+            }
+            __syncwarp();
+            if (lane < m - 1) {
+                const double2 v = sm.s[sm.rem[lane]][p];
+                const double2 l = make_double2(v.x * irt, v.y * irt);
+                sm.pc[lane] = l;
+                sm.lc[t][sm.rem[lane]] = l;
+            }
+            __syncwarp();
+            for (int e = lane; e < (m - 1) * m / 2; e += 32) {        // Schur update, packed lower triangle
+                int ia, ib;
+                tri_index(e, ia, ib);
+                const int ua = sm.rem[ia], ub = sm.rem[ib];
+                const double2 pr = zmul(sm.pc[ia], zconj(sm.pc[ib]));
+                const double2 v = make_double2(sm.s[ua][ub].x - pr.x, sm.s[ua][ub].y - pr.y);
+                sm.s[ua][ub] = v;
+                sm.s[ub][ua] = zconj(v);
+            }
+            __syncwarp();
+        }
+
+        if (!singular) {
+            for (int e = lane; e < K * K; e += 32) {                    // R in level order
+                const int r = e / K, q = e % K;
+                sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
+            }
+            __syncwarp();
+            for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = make_double2(0.0, 0.0);
+            __syncwarp();
+            // U = R^-1 by rows from the bottom: U_m. = (e_m - sum_{j>m} R_mj U_j.) / R_mm
+            for (int m = K - 1; m >= 0; --m) {
+                if (lane < K) {
+                    const int k = lane;
+                    const double2 acc = sm.lc[m][k];
+                    const double ri = sm.rinv[m];
+                    sm.u[m][k] = (k < m) ? make_double2(0.0, 0.0)
+                                         : make_double2(((k == m ? 1.0 : 0.0) - acc.x) * ri, -acc.y * ri);
+                }
+                __syncwarp();
+                const int w = K - m;                                    // entries (i < m, k >= m)
+                for (int e = lane; e < m * w; e += 32) {
+                    const int i = e / w, k = m + e % w;
+                    sm.lc[i][k] = zfma(sm.r[i][m], sm.u[m][k], sm.lc[i][k]);
+                }
+                __syncwarp();
+            }
+            // one Newton step: E = I - R U, U2 = U + U E (both upper triangular), accumulated by rank-1 steps
+            for (int e = lane; e < K * K; e += 32) {
+                const int r = e / K, q = e % K;
+                sm.s[r][q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
+            }
+            __syncwarp();
+            for (int m = 0; m < K; ++m) {                               // E_ik -= R_im U_mk, i <= m <= k
+                const int w = K - m;
+                for (int e = lane; e < (m + 1) * w; e += 32) {
+                    const int i = e / w, k = m + e % w;
+                    const double2 pr = zmul(sm.r[i][m], sm.u[m][k]);
+                    sm.s[i][k].x -= pr.x;
+                    sm.s[i][k].y -= pr.y;
+                }
+                __syncwarp();
+            }
+            for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = sm.u[e / K][e % K];
+            __syncwarp();
+            for (int m = 0; m < K; ++m) {                               // U2_ik += U_im E_mk, i <= m <= k
+                const int w = K - m;
+                for (int e = lane; e < (m + 1) * w; e += 32) {
+                    const int i = e / w, k = m + e % w;
+                    sm.lc[i][k] = zfma(sm.u[i][m], sm.s[m][k], sm.lc[i][k]);
+                }
+                __syncwarp();
+            }
+            // U2 (in lc) as FP32 hi + lo; outputs: row r of U~, w_r, user of level r
+            if (lane < K) sm.rd[lane] = 1.0 / sm.lc[lane][lane].x;     // 1 / U2_rr
+            __syncwarp();
+            for (int e = lane; e < K * K; e += 32) {
+                const int r = e / K, q = e % K;
+                const double2 v = sm.lc[r][q];
+                const float hx = (float)v.x, hy = (float)v.y;
+                sm.uh[r][q] = make_float2(hx, hy);
+                sm.ul[r][q] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+                const double urr = sm.lc[r][r].x, iurr = sm.rd[r];
+                const float2 ut = (q > r) ? make_float2((float)(v.x * iurr), (float)(v.y * iurr))
+                                          : (q == r ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
+                f.s.utp[r * K + q] = make_float4(ut.x, ut.y, ut.y, ut.x);
+                f.s.utc[q * K + r] = ut;
+                if (f.U_out) f.U_out[r * K + q] = make_float2(hx, hy);
+                if (q == 0) {
+                    f.s.w[r] = (float)(urr * urr);
+                    f.s.ul[r] = (uint8_t)sm.uol[r];
+                    if (f.ul_out) f.ul_out[r] = (uint8_t)sm.uol[r];
+                }
+            }
+            __syncwarp();
+            // A = U2^H U2 (Hermitian) in compensated FP32: A_ik = sum_{m <= min(i,k)} conj(U2_mi) U2_mk
+            for (int e = lane; e < K * (K + 1) / 2; e += 32) {
+                int i, k;
+                tri_index(e, i, k);                                     // i >= k
+                float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
+                for (int m = 0; m <= k; ++m) {
+                    const float2 xh = sm.uh[m][i], xl = sm.ul[m][i];
+                    const float2 cx = make_float2(xh.x, -xh.y);
+                    cdot2(cx, sm.uh[m][k], sm.ul[m][k], re, ree, im, ime);
+                    ree = fmaf(xl.x, sm.uh[m][k].x, fmaf(xl.y, sm.uh[m][k].y, ree));    // conj(xl) * yh
+                    ime = fmaf(xl.x, sm.uh[m][k].y, fmaf(-xl.y, sm.uh[m][k].x, ime));
+                }
+                const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
+                const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
+                sm.ahi[i][k] = hi;
+                sm.alo[i][k] = lo;
+                sm.ahi[k][i] = make_float2(hi.x, -hi.y);
+                sm.alo[k][i] = make_float2(lo.x, -lo.y);
+            }
+            __syncwarp();
+            // P_level[m][k] = sum_j conj(H_perm[j][m]) A[j][k], compensated FP32
+            for (int e = lane; e < M * K; e += 32) {
+                const int m = e / K, k = e % K;
+                float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
+                for (int j = 0; j < K; ++j) {
+                    const float2 hv = sm.h[sm.uol[j]][m];
+                    cdot2(make_float2(hv.x, -hv.y), sm.ahi[j][k], sm.alo[j][k], re, ree, im, ime);
+                }
+                const float2 hi = make_float2(__fadd_rn(re, ree), __fadd_rn(im, ime));
+                const float2 lo = make_float2(__fsub_rn(ree, __fsub_rn(hi.x, re)), __fsub_rn(ime, __fsub_rn(hi.y, im)));
+                const int uk = sm.uol[k];
+                f.s.pt[uk * Mp + m] = hi;
+                f.s.ptlo[uk * Mp + m] = lo;
+                if (f.P_out) f.P_out[m * K + uk] = hi;
+            }
+            // regularisation rows (lambda > 0): row M + u of P is lambda A[level of u][.]
+            for (int e = lane; e < (Mp - M) * K; e += 32) {
+                const int u = e / K, k = e % K;
+                int lu = 0;
+                for (int i = 0; i < K; ++i) lu = (sm.uol[i] == u) ? i : lu;
+                const float2 ah = sm.ahi[lu][k], al = sm.alo[lu][k];
+                float hx, ex, hy, ey;
+                two_prod(lam, ah.x, hx, ex);
+                two_prod(lam, ah.y, hy, ey);
+                const int uk = sm.uol[k];
+                f.s.pt[uk * Mp + M + u] = make_float2(hx, hy);
+                f.s.ptlo[uk * Mp + M + u] = make_float2(fmaf(lam, al.x, ex), fmaf(lam, al.y, ey));
+            }
+            if (lane == 0) f.s.st[0] = (uint8_t)VP_CH_FP64;
+        } else {
+            if (lane < 16) write_channel_outputs_zero(f, K, M, Mp, lane);
+            if (lane == 0) f.s.st[0] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
+        }
+        __syncwarp();
     }
-    // one channel per warp, spread over the blocks first (so that every SM gets its share)
-    for (int slot = blockIdx.x + gridDim.x * warp; slot < nflag; slot += gridDim.x * 4)
-        fp64_channel<32>(a, smem[warp], a.flags[slot], lane);
 }
 
 FactorArgs make_args(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out, uint8_t* ul_out)
@@ -687,14 +663,10 @@ cudaError_t run_factor32(const FactorArgs& a, cudaStream_t s)
 
 cudaError_t run_factor64(const FactorArgs& a, int max_flagged, cudaStream_t s)
 {
-    // 4 warps and 4 channel workspaces per block, 2 blocks per SM
-    int blocks = (max_flagged + 3) / 4;
-    if (blocks > 152 * 2) blocks = 152 * 2;
+    int blocks = (max_flagged + kW64 - 1) / kW64;
+    if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    const size_t sh = 4 * sizeof(Smem64);
-    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(factor64_kernel), sh);
-    if (e != cudaSuccess) return e;
-    factor64_kernel<<<blocks, 128, sh, s>>>(a);
+    factor64_kernel<<<blocks, 32 * kW64, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,8 @@ def drain_all(srv, timeout=20.0):
 
 
 def test_jobs_complete_and_are_reported_once():
-    with vp.Server(64 << 20, lanes=3, fake=True) as srv:
-        ids = [srv.submit(job(C)) for C in (200, 300, 100, 50, 400, 80)]
+    with vp.Server(1 << 30, lanes=3, fake=True) as srv:        # host bookkeeping only
+        ids = [srv.submit(job(C)) for C in (2000, 3000, 1000, 500, 4000, 800)]
         done = drain_all(srv)
         assert sorted(r[0] for r in done) == sorted(ids)
         assert all(r[1] == 0 and 0.0 <= r[2] <= r[3] for r in done)
@@ -59,12 +59,12 @@ def test_admission_waits_for_pool_space_first_come():
     """A job that does not fit waits at the head of the queue and the jobs
     behind it wait too (first come, first served), until space frees up."""
     unit = per_channel_bytes()
-    pool = 1000 * unit + (1 << 20)
+    pool = 10000 * unit + (1 << 20)
     with vp.Server(pool, lanes=4, fake=True) as srv:
         srv.reset_clock()
-        a = srv.submit(job(600))        # 600 us, 600 channels of state
-        b = srv.submit(job(700))        # does not fit beside a: waits
-        c = srv.submit(job(10))         # would fit, but queues behind b
+        a = srv.submit(job(6000))       # 6 ms, 6000 channels of state
+        b = srv.submit(job(7000))       # does not fit beside a: waits
+        c = srv.submit(job(100))        # would fit, but queues behind b
         st = srv.stats()
         assert st["in_flight"] == 1 and st["queued"] == 2
         done = {r[0]: r for r in drain_all(srv)}
@@ -75,14 +75,14 @@ def test_admission_waits_for_pool_space_first_come():
 
 def test_pool_accounting_coalesces():
     unit = per_channel_bytes()
-    with vp.Server(100 * unit + (1 << 20), lanes=8, fake=True) as srv:
+    with vp.Server(8000 * unit + (1 << 20), lanes=8, fake=True) as srv:
         for _ in range(4):
-            srv.submit(job(25))
+            srv.submit(job(2000))                   # 2 ms each: all four still running below
         st = srv.stats()
-        assert st["in_flight"] == 4 and st["pool_used"] >= 4 * 25 * unit
+        assert st["in_flight"] == 4 and st["pool_used"] >= 4 * 2000 * unit
         drain_all(srv)
         # freed pieces merge back: a job of nearly the whole pool fits again
-        srv.submit(job(100))
+        srv.submit(job(8000))
         assert srv.stats()["in_flight"] == 1
         drain_all(srv)
         assert srv.stats()["pool_used"] == 0
