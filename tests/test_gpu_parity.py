@@ -216,3 +216,42 @@ def test_small_budgets_several_vectors_per_warp(orc, K, M, qam, n, S):
     assert np.array_equal(x.cpu().numpy().reshape(C * S, M), gpu["x"])
     assert np.array_equal(l.cpu().numpy().reshape(C * S, K, 2), gpu["l"])
     assert np.array_equal(g.cpu().numpy().astype(np.float64), gpu["gamma"])
+
+
+def test_concurrent_plans_on_two_streams_equal_sequential():
+    """Two plans launched on two streams at once give the same bits as the
+    same calls one after another, and a repeated run gives the same bits."""
+    dev = torch.device("cuda:0")
+    runs = []
+    for wl, sub in ((W.SLOT_16x16, 96), (W.RB_8x8, 12 * 20)):
+        b = W.make_batch(wl, subcarriers=sub)
+        C, K, M = b.H.shape
+        V = b.sym.shape[0]
+        runs.append((wl, b, torch.from_numpy(b.H).to(dev), torch.from_numpy(b.sym).to(dev),
+                     torch.from_numpy(b.vec_off).to(dev), C, K, M, V))
+
+    def outputs(streams):
+        res = []
+        plans = []
+        for (wl, b, H, sym, off, C, K, M, V), st in zip(runs, streams):
+            x = torch.empty((V, M), dtype=torch.complex64, device=dev)
+            l = torch.empty((V, K, 2), dtype=torch.int8, device=dev)
+            g = torch.empty((V,), dtype=torch.float32, device=dev)
+            p = vp.Plan(K, M, wl.qam, wl.n_paths)
+            plans.append(p)
+            vp.vp_factorize(p.handle, H, C, stream=st)
+            vp.vp_precode(p.handle, sym, 0, off, V, x, l, g, stream=st)
+            res.append((x, l, g))
+        torch.cuda.synchronize()
+        out = [tuple(t.cpu().numpy() for t in r) for r in res]
+        for p in plans:
+            p.close()
+        return out
+
+    seq = outputs([None, None])
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    conc = outputs([s1, s2])
+    again = outputs([s2, s1])
+    for a, b, c in zip(seq, conc, again):
+        for u, v, w in zip(a, b, c):
+            assert np.array_equal(u, v) and np.array_equal(u, w)
