@@ -8,7 +8,7 @@
 // registers in units of tau (r' = r / tau is the effective point s_hat_l of
 // Eq. (17)); choosing t_l at level l updates them column-wise,
 //   r'_m -= U~_ml t_l,  m < l,
-// with two packed FP32 FMAs per complex term, and t_l is the p_l-th nearest point of
+// one packed FP32 add per complex term from a per-block table of -U~_ml t, and t_l is the p_l-th nearest point of
 // {-1,0,1}+j{-1,0,1} to r'_l (DEMAP), ties to the smaller (Re t, Im t).
 // The PED grows by w_l tau^2 |r'_l - t_l|^2.
 // The zero perturbation is candidate 0; the warp's (PED, index) minimum wins
@@ -224,8 +224,50 @@ __device__ void build_lut(uint64_t* lut)
     }
 }
 
+// Column table of the descent. The column update r'_m -= U~_m,lv t has only
+// nine possible right-hand sides per (m, lv), one per alphabet point t, so
+// each block tabulates them once: entry (lv, k, m) = -U~_m,lv t for the 4-bit
+// point code k = (Re t + 1) | (Im t + 1) << 2 (the code recorded for the
+// path; 0..10, 3 and 7 unused) and m < lv. A lane's update is then one
+// shared load and one packed add per row, the load's address depending on
+// its own t. Row stride lv | 1 (odd, in float2 units): the nine codes of a
+// warp then fall on distinct bank pairs (k * stride mod 16 differs for
+// distinct k < 16).
+__host__ __device__ constexpr int ct_stride(int lv) { return lv | 1; }
+__host__ __device__ constexpr int ct_off(int lv)
+{
+    int o = 0;
+    for (int j = 1; j < lv; ++j) o += 11 * ct_stride(j);
+    return o;
+}
+__host__ __device__ constexpr int ct_size(int KT) { return ct_off(KT); }   // float2 entries, levels 1..KT-1
+
+// Fills the block's column table from U~ as (re, im, im, re)-packed float4
+// [K][K] (level order): one pass over U~, a thread per entry above the
+// diagonal writing its nine codes. Only those entries are ever read (valid
+// codes, m < lv < K). FIX rounds the entries of U~ to words first, so a table
+// entry (the sum of two words) is exact.
+template <bool FIX>
+__device__ void build_ctab(float2* ctab, const float4* utp_g, int K, const FixP& fx)
+{
+    for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
+        const int m = i / K, lv = i - m * K;
+        if (m >= lv) continue;
+        float4 u = utp_g[i];
+        if (FIX) u = make_float4(qword(u.x, fx), qword(u.y, fx), qword(u.z, fx), qword(u.w, fx));
+        float2* e = ctab + ct_off(lv) + m;
+        const int st = ct_stride(lv);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {                  // alphabet point a = 3 (tr + 1) + (ti + 1)
+            const float tr = (float)(a / 3 - 1), ti = (float)(a % 3 - 1);
+            const int k = (a / 3) | ((a % 3) << 2);
+            e[k * st] = make_float2(fmaf(u.z, ti, -tr * u.x), fmaf(u.w, -ti, -tr * u.y));
+        }
+    }
+}
+
 template <int KT, bool LUT, bool FIX>
-__device__ __forceinline__ void level_step(int lv, const float4* utp, const float* wv, uint32_t cw0, uint32_t cw1,
+__device__ __forceinline__ void level_step(int lv, const float2* ctab, const float* wv, uint32_t cw0, uint32_t cw1,
                                            uint32_t mq0, uint32_t mq1, const uint64_t* lut, const FixP& fx,
                                            float2 (&r)[KT], float& ped, uint32_t& lc0, uint32_t& lc1)
 {
@@ -243,17 +285,15 @@ __device__ __forceinline__ void level_step(int lv, const float4* utp, const floa
     const float ftr = (float)tr, fti = (float)ti;
     const float dx = cx - ftr, dy = cy - fti;
     ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
-    const uint32_t dig = (uint32_t)((tr + 1) | ((ti + 1) << 2)) << sh;
+    const int kd = (tr + 1) | ((ti + 1) << 2);
+    const uint32_t dig = (uint32_t)kd << sh;
     if (lv < 8) lc0 |= dig; else lc1 |= dig;
     if (lv > 0) {
-        const float2 c1 = make_float2(-ftr, -ftr);
-        const float2 c2 = make_float2(fti, -fti);
+        const float2* col = ctab + ct_off(lv) + kd * ct_stride(lv);
 #pragma unroll
         for (int m = 0; m < KT; ++m) {
             if (m < lv) {
-                const float4 u = utp[m * KT + lv];
-                r[m] = __ffma2_rn(make_float2(u.x, u.y), c1, r[m]);
-                r[m] = __ffma2_rn(make_float2(u.z, u.w), c2, r[m]);
+                r[m] = __fadd2_rn(r[m], col[m]);
                 if (FIX) {
                     r[m].x = fminf(fmaxf(r[m].x, -fx.lim), fx.lim);
                     r[m].y = fminf(fmaxf(r[m].y, -fx.lim), fx.lim);
@@ -312,28 +352,34 @@ __host__ __device__ inline int take16(int& o, int bytes)
 
 
 // Shared-memory layout of one search block (byte offsets, 16-byte aligned).
+// The paths' codes and meta words are staged as well, unless gp (the block
+// reads them in place from global memory, once per 32-path chunk; tc = meta
+// = -1): the launch chooses gp when staging them would leave fewer than four
+// blocks on an SM, the register limit of the launch bounds.
+constexpr int kSearchSmemBudget = 57344;   // (228 KB per SM) / 4 - 1 KB reserved per block
+
 struct SearchSmem {
-    int utp, utc, pt, ptl, bvec, scr, tc, tmq, pcode, lut, scrl, scrp, wv, ulv, meta, total;
+    int ctab, utc, pt, ptl, bvec, scr, tmq, pcode, lut, scrl, scrp, wv, ulv, tc, meta, total;
 };
 
-__host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW)
+__host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW, bool gp)
 {
     SearchSmem s;
     int o = 0;
-    s.utp = take16(o, 16 * KT * KT);
+    s.ctab = take16(o, 8 * ct_size(KT));
     s.utc = take16(o, 8 * KT * KT);
     s.pt = take16(o, 8 * KM);
     s.ptl = take16(o, 8 * KM);
     s.bvec = take16(o, 8 * NW * KT);
     s.scr = take16(o, 8 * NW * KT * kMaxPrefix);
-    s.tc = take16(o, 8 * NP);
+    s.tc = gp ? -1 : take16(o, 8 * NP);
     s.tmq = take16(o, 8 * n_chunks(NP));
     s.pcode = take16(o, 8 * kMaxPrefix);
     s.scrl = take16(o, 8 * NW * kMaxPrefix);
     s.scrp = take16(o, 4 * NW * kMaxPrefix);
     s.wv = take16(o, 4 * KT);
     s.ulv = take16(o, 4 * KT);
-    s.meta = take16(o, 4 * NP);
+    s.meta = gp ? -1 : take16(o, 4 * NP);
     s.lut = take16(o, 8 * 72);
     s.total = o;
     return s;
@@ -347,7 +393,7 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
 // then continues from its prefix's state through the remaining levels. The
 // arithmetic per path is the same as a full descent, so results are
 // identical; the shared levels are the ones with the most column updates.
-template <int KT, bool BATCH, bool LUT, bool FIX>
+template <int KT, bool BATCH, bool LUT, bool FIX, bool GP>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -383,21 +429,22 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         sym = a.sym; xo = a.x; lo = a.l; go = a.gamma;
     }
     const int KM = BATCH ? a.KM : K * Mp, NP = BATCH ? a.NP : n;
-    const SearchSmem L = search_smem(KT, KM, NP, NW);
-    float4* utp = reinterpret_cast<float4*>(smraw + L.utp);        // [KT][KT]
+    const SearchSmem L = search_smem(KT, KM, NP, NW, GP);
+    float2* ctab = reinterpret_cast<float2*>(smraw + L.ctab);      // column table
     float2* utc = reinterpret_cast<float2*>(smraw + L.utc);        // [KT][KT]
     float2* pt = reinterpret_cast<float2*>(smraw + L.pt);          // [K][M] leading part of P^T
     float2* ptl = reinterpret_cast<float2*>(smraw + L.ptl);        // [K][M] trailing part
     float2* bvec = reinterpret_cast<float2*>(smraw + L.bvec);      // [NW][KT]
     float2* scr_all = reinterpret_cast<float2*>(smraw + L.scr);    // [NW][KT][32] prefix residuals
-    uint64_t* tc = reinterpret_cast<uint64_t*>(smraw + L.tc);      // [n] codes, evaluation order
+    // [n] codes in evaluation order and their MoP rank | prefix << 16 (staged unless GP)
+    uint64_t* tc = GP ? nullptr : reinterpret_cast<uint64_t*>(smraw + L.tc);
+    uint32_t* meta = GP ? nullptr : reinterpret_cast<uint32_t*>(smraw + L.meta);
     uint64_t* tmq = reinterpret_cast<uint64_t*>(smraw + L.tmq);    // [nch] chunk digit maxima, evaluation order
     uint64_t* pcode = reinterpret_cast<uint64_t*>(smraw + L.pcode);// [32] a code of each prefix
     uint2* scrl_all = reinterpret_cast<uint2*>(smraw + L.scrl);    // [NW][32] prefix chosen points
     float* scrp_all = reinterpret_cast<float*>(smraw + L.scrp);    // [NW][32] prefix PED
     float* wv = reinterpret_cast<float*>(smraw + L.wv);            // [KT]
     int* ulv = reinterpret_cast<int*>(smraw + L.ulv);              // [KT]
-    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + L.meta);  // [n] MoP rank | prefix << 16
     uint64_t* lut = reinterpret_cast<uint64_t*>(smraw + L.lut);    // [72] region lists (LUT DEMAP)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -417,23 +464,21 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
         const int r = i / KT, q = i % KT;
         const bool in = r < K && q < K;
-        float4 u = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         float2 uc = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
-        if (FIX) {
-            u = make_float4(qword(u.x, fx), qword(u.y, fx), qword(u.z, fx), qword(u.w, fx));
-            uc = make_float2(qword(uc.x, fx), qword(uc.y, fx));
-        }
-        utp[i] = u;
+        if (FIX) uc = make_float2(qword(uc.x, fx), qword(uc.y, fx));
         utc[i] = uc;
     }
+    build_ctab<FIX>(ctab, cs.utp, K, fx);
     for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
         pt[i] = cs.pt[i];
         ptl[i] = cs.ptlo[i];
     }
     // evaluation order, shared prefixes and chunk digit maxima (from path selection)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        tc[i] = cs.ecode[i];
-        meta[i] = cs.emeta[i];
+    if (!GP) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            tc[i] = cs.ecode[i];
+            meta[i] = cs.emeta[i];
+        }
     }
     for (int i = threadIdx.x; i < nch; i += blockDim.x) tmq[i] = cs.maxq[i];
     for (int i = threadIdx.x; i < kMaxPrefix; i += blockDim.x) pcode[i] = cs.pcode[i];
@@ -494,7 +539,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
                 for (int lv = KT - 1; lv >= kLo; --lv) {
                     if (lv >= KT - T)
-                        level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, fx,
+                        level_step<KT, LUT, FIX>(lv, ctab, wv, cw0, cw1, (uint32_t)amq, (uint32_t)(amq >> 32), lut, fx,
                                                  r, ped, lc0, lc1);
                 }
                 if (lane < NPF) {
@@ -513,9 +558,9 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
             for (int ch = 0; ch < nch; ++ch) {
                 const int jp = ch * 32 + lane;
                 const bool vld = jp < n;
-                const uint64_t code = vld ? tc[jp] : 0ull;
+                const uint64_t code = !vld ? 0ull : (GP ? __ldg(cs.ecode + jp) : tc[jp]);
                 const uint32_t cw0 = (uint32_t)code, cw1 = (uint32_t)(code >> 32);
-                const uint32_t mt = vld ? meta[jp] : 0u;
+                const uint32_t mt = !vld ? 0u : (GP ? __ldg(cs.emeta + jp) : meta[jp]);
                 const int rk = vld ? (int)(mt & 0xffffu) : 0x7fffffff;
                 const int p = (int)(mt >> 16);
                 const uint64_t mq = tmq[ch];
@@ -528,7 +573,7 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 #pragma unroll
                 for (int lv = KT - 1; lv >= 0; --lv) {
                     if (lv < KB)
-                        level_step<KT, LUT, FIX>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, fx,
+                        level_step<KT, LUT, FIX>(lv, ctab, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), lut, fx,
                                                  r, ped, lc0, lc1);
                 }
                 if (vld && (ped < bp || (ped == bp && rk < brk))) { bp = ped; brk = rk; blc0 = lc0; blc1 = lc1; }
@@ -585,14 +630,14 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 
 // Shared-memory layout of the one-pass search (byte offsets, 16-byte aligned).
 struct SmallSmem {
-    int utp, utc, pt, ptl, tc, meta, wv, ulv, bw, sv, g0, wins, total;
+    int ctab, utc, pt, ptl, tc, meta, wv, ulv, bw, sv, g0, wins, total;
 };
 
 __host__ __device__ inline SmallSmem small_smem(int KT, int KM, int NW, int G)
 {
     SmallSmem s;
     int o = 0;
-    s.utp = take16(o, 16 * KT * KT);
+    s.ctab = take16(o, 8 * ct_size(KT));
     s.utc = take16(o, 8 * KT * KT);
     s.pt = take16(o, 8 * KM);
     s.ptl = take16(o, 8 * KM);
@@ -636,7 +681,7 @@ __global__ void __launch_bounds__(224, 4) search_small_kernel(SearchArgs a)
     int8_t* lo = a.l;
     float* go = a.gamma;
     const SmallSmem L = small_smem(KT, K * Mp, NW, G);
-    float4* utp = reinterpret_cast<float4*>(smraw + L.utp);        // [KT][KT]
+    float2* ctab = reinterpret_cast<float2*>(smraw + L.ctab);      // column table
     float2* utc = reinterpret_cast<float2*>(smraw + L.utc);        // [KT][KT]
     float2* pt = reinterpret_cast<float2*>(smraw + L.pt);          // [K][Mp]
     float2* ptl = reinterpret_cast<float2*>(smraw + L.ptl);
@@ -664,7 +709,6 @@ __global__ void __launch_bounds__(224, 4) search_small_kernel(SearchArgs a)
     for (int i = threadIdx.x; i < KT * KT; i += blockDim.x) {
         const int r = i / KT, q = i % KT;
         const bool in = r < K && q < K;
-        utp[i] = in ? cs.utp[r * K + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         utc[i] = in ? cs.utc[r * K + q] : make_float2(0.f, 0.f);
     }
     for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
@@ -681,6 +725,7 @@ __global__ void __launch_bounds__(224, 4) search_small_kernel(SearchArgs a)
     }
     const uint64_t mq = cs.maxq[0];                   // one chunk: digit maxima of all paths
     const FixP fx = FixP();
+    build_ctab<false>(ctab, cs.utp, K, fx);
     __syncthreads();
 
     const int g = lane / P, p = lane % P;
@@ -723,7 +768,7 @@ __global__ void __launch_bounds__(224, 4) search_small_kernel(SearchArgs a)
 #pragma unroll
         for (int lv = KT - 1; lv >= 0; --lv) {
             if (lv < K)
-                level_step<KT, false, false>(lv, utp, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), nullptr, fx,
+                level_step<KT, false, false>(lv, ctab, wv, cw0, cw1, (uint32_t)mq, (uint32_t)(mq >> 32), nullptr, fx,
                                              r, ped, lc0, lc1);
         }
         const float bp = vld ? ped : INFINITY;
@@ -793,25 +838,38 @@ cudaError_t launch_small_kt(const SearchArgs& a, int C, int per, cudaStream_t s)
     return launch_small<KT, 2>(a, C, per, s);
 }
 
-template <int KT, bool BATCH, bool LUT, bool FIX>
-cudaError_t launch_one(const SearchArgs& a, int C, int threads, size_t sh, cudaStream_t s)
+template <int KT, bool BATCH, bool LUT, bool FIX, bool GP>
+cudaError_t launch_one(const SearchArgs& a, int C, int threads, int KM, int NP, cudaStream_t s)
 {
-    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_kernel<KT, BATCH, LUT, FIX>), sh);
+    const size_t sh = (size_t)search_smem(KT, KM, NP, threads / 32, GP).total;
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_kernel<KT, BATCH, LUT, FIX, GP>), sh);
     if (e != cudaSuccess) return e;
-    search_kernel<KT, BATCH, LUT, FIX><<<C, threads, sh, s>>>(a);
+    search_kernel<KT, BATCH, LUT, FIX, GP><<<C, threads, sh, s>>>(a);
     return cudaGetLastError();
+}
+
+// Paths read in place (GP) where staging them would cost occupancy: only the
+// 16-level tile can get there (n up to 1024, or P with the K rows of
+// lambda > 0), and only its plain and batch forms have the GP variant; the
+// study variants keep the staged layout with fewer blocks per SM.
+template <int KT, bool BATCH, bool LUT, bool FIX>
+cudaError_t launch_gp(const SearchArgs& a, int C, int threads, int KM, int NP, cudaStream_t s)
+{
+    if constexpr (KT == 16 && !LUT && !FIX) {
+        if (search_smem(KT, KM, NP, threads / 32, false).total > kSearchSmemBudget)
+            return launch_one<KT, BATCH, LUT, FIX, true>(a, C, threads, KM, NP, s);
+    }
+    return launch_one<KT, BATCH, LUT, FIX, false>(a, C, threads, KM, NP, s);
 }
 
 template <int KT>
 cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
 {
-    const int NW = threads / 32;
     const int KM = a.probs ? a.KM : a.K * a.Mp, NP = a.probs ? a.NP : a.n;
-    const size_t sh = (size_t)search_smem(KT, KM, NP, NW).total;
-    if (a.probs) return launch_one<KT, true, false, false>(a, C, threads, sh, s);
-    if (a.frac > 0) return launch_one<KT, false, false, true>(a, C, threads, sh, s);
-    if (a.demap == VP_DEMAP_LUT) return launch_one<KT, false, true, false>(a, C, threads, sh, s);
-    return launch_one<KT, false, false, false>(a, C, threads, sh, s);
+    if (a.probs) return launch_gp<KT, true, false, false>(a, C, threads, KM, NP, s);
+    if (a.frac > 0) return launch_gp<KT, false, false, true>(a, C, threads, KM, NP, s);
+    if (a.demap == VP_DEMAP_LUT) return launch_gp<KT, false, true, false>(a, C, threads, KM, NP, s);
+    return launch_gp<KT, false, false, false>(a, C, threads, KM, NP, s);
 }
 
 }  // namespace

@@ -255,3 +255,23 @@ def test_concurrent_plans_on_two_streams_equal_sequential():
     for a, b, c in zip(seq, conc, again):
         for u, v, w in zip(a, b, c):
             assert np.array_equal(u, v) and np.array_equal(u, w)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.3])
+def test_maximum_path_budget_16x16(orc, lam):
+    """n = VP_MAX_PATHS at the 16-level tile (32 chunks of 32 paths, shared
+    prefixes), ragged vector counts per channel, with and without the K
+    regularisation rows of P: the launch then reads the paths from global
+    memory instead of staging them (four blocks per SM)."""
+    K = M = 16
+    n = vp.VP_MAX_PATHS
+    rng = W.rng_for(73, int(lam * 10))
+    C = 10
+    H = W.channels(rng, C, K, M, "kron", 0.5, 0.2)
+    counts = rng.integers(0, 5, C)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    sym = W.symbols(rng, int(off[-1]), K, 256)
+    gpu = run_gpu(H, sym, off, 256, n, lam=lam)
+    ref = orc.precode_batch(H, sym, off, 256, n, lam=lam, nthreads=orc.max_threads())
+    assert np.array_equal(gpu["status"] & 3, ref["status"])
+    assert_parity(compare(orc, H, sym, off, 256, gpu, ref, lam=lam))
