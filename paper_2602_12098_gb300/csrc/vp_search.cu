@@ -285,9 +285,11 @@ __device__ __forceinline__ void level_step(int lv, const float2* ctab, const flo
     const float ftr = (float)tr, fti = (float)ti;
     const float dx = cx - ftr, dy = cy - fti;
     ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
-    const int kd = (tr + 1) | ((ti + 1) << 2);
+    // point code (tr + 1) | (ti + 1) << 2, written as a sum, and recorded by an
+    // add (the level's nibble is still zero): both fuse into multiply-adds
+    const int kd = tr + 4 * ti + 5;
     const uint32_t dig = (uint32_t)kd << sh;
-    if (lv < 8) lc0 |= dig; else lc1 |= dig;
+    if (lv < 8) lc0 += dig; else lc1 += dig;
     if (lv > 0) {
         const float2* col = ctab + ct_off(lv) + kd * ct_stride(lv);
 #pragma unroll
