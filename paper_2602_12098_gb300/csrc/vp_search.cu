@@ -228,24 +228,24 @@ __device__ void build_lut(uint64_t* lut)
 // nine possible right-hand sides per (m, lv), one per alphabet point t, so
 // each block tabulates them once: entry (lv, k, m) = -U~_m,lv t for the 4-bit
 // point code k = (Re t + 1) | (Im t + 1) << 2 (the code recorded for the
-// path; 0..10, 3 and 7 unused) and m < lv. A lane's update is then one
-// shared load and one packed add per row, the load's address depending on
-// its own t. Row stride lv | 1 (odd, in float2 units): the nine codes of a
-// warp then fall on distinct bank pairs (k * stride mod 16 differs for
-// distinct k < 16).
-__host__ __device__ constexpr int ct_stride(int lv) { return lv | 1; }
+// path; 0..10, 3 and 7 unused) and m < lv, and entry (lv, k, lv) = -t itself
+// (for the PED's r'_lv - t). A lane's update is then one shared load and one
+// packed add per row, the load's address depending on its own t. Row stride
+// (lv + 1) | 1 (odd, in float2 units): the nine codes of a warp then fall on
+// distinct bank pairs (k * stride mod 16 differs for distinct k < 16).
+__host__ __device__ constexpr int ct_stride(int lv) { return (lv + 1) | 1; }
 __host__ __device__ constexpr int ct_off(int lv)
 {
     int o = 0;
-    for (int j = 1; j < lv; ++j) o += 11 * ct_stride(j);
+    for (int j = 0; j < lv; ++j) o += 11 * ct_stride(j);
     return o;
 }
-__host__ __device__ constexpr int ct_size(int KT) { return ct_off(KT); }   // float2 entries, levels 1..KT-1
+__host__ __device__ constexpr int ct_size(int KT) { return ct_off(KT); }   // float2 entries, levels 0..KT-1
 
 // Fills the block's column table from U~ as (re, im, im, re)-packed float4
 // [K][K] (level order): one pass over U~, a thread per entry above the
-// diagonal writing its nine codes. Only those entries are ever read (valid
-// codes, m < lv < K). FIX rounds the entries of U~ to words first, so a table
+// diagonal writing its nine codes, then the points -t at m = lv. Only those
+// entries are ever read (valid codes, m <= lv < K). FIX rounds the entries of U~ to words first, so a table
 // entry (the sum of two words) is exact.
 template <bool FIX>
 __device__ void build_ctab(float2* ctab, const float4* utp_g, int K, const FixP& fx)
@@ -263,6 +263,11 @@ __device__ void build_ctab(float2* ctab, const float4* utp_g, int K, const FixP&
             const int k = (a / 3) | ((a % 3) << 2);
             e[k * st] = make_float2(fmaf(u.z, ti, -tr * u.x), fmaf(u.w, -ti, -tr * u.y));
         }
+    }
+    for (int i = threadIdx.x; i < 9 * K; i += blockDim.x) {   // -t itself, at m = lv
+        const int lv = i / 9, a = i - 9 * lv;
+        const int k = (a / 3) | ((a % 3) << 2);
+        ctab[ct_off(lv) + k * ct_stride(lv) + lv] = make_float2((float)(1 - a / 3), (float)(1 - a % 3));
     }
 }
 
@@ -282,16 +287,15 @@ __device__ __forceinline__ void level_step(int lv, const float2* ctab, const flo
         if (FIX) select_point(cx, cy, q, mql, tr, ti, fx.epsx, fx.epsy);
         else select_point(cx, cy, q, mql, tr, ti);
     }
-    const float ftr = (float)tr, fti = (float)ti;
-    const float dx = cx - ftr, dy = cy - fti;
-    ped = fmaf(wv[lv], fmaf(dx, dx, dy * dy), ped);
     // point code (tr + 1) | (ti + 1) << 2, written as a sum, and recorded by an
     // add (the level's nibble is still zero): both fuse into multiply-adds
     const int kd = tr + 4 * ti + 5;
     const uint32_t dig = (uint32_t)kd << sh;
     if (lv < 8) lc0 += dig; else lc1 += dig;
+    const float2* col = ctab + ct_off(lv) + kd * ct_stride(lv);
+    const float2 d = __fadd2_rn(r[lv], col[lv]);                 // r'_lv - t
+    ped = fmaf(wv[lv], fmaf(d.x, d.x, d.y * d.y), ped);
     if (lv > 0) {
-        const float2* col = ctab + ct_off(lv) + kd * ct_stride(lv);
 #pragma unroll
         for (int m = 0; m < KT; ++m) {
             if (m < lv) {
