@@ -8,8 +8,9 @@
 // registers in units of tau (r' = r / tau is the effective point s_hat_l of
 // Eq. (17)); choosing t_l at level l updates them column-wise,
 //   r'_m -= U~_ml t_l,  m < l,
-// one packed FP32 add per complex term from a per-block table of -U~_ml t, and t_l is the p_l-th nearest point of
-// {-1,0,1}+j{-1,0,1} to r'_l (DEMAP), ties to the smaller (Re t, Im t).
+// one packed FP32 add per complex term from a per-block table of -U~_ml t,
+// and t_l is the p_l-th nearest point of {-1,0,1}+j{-1,0,1} to r'_l (DEMAP),
+// ties to the smaller (Re t, Im t).
 // The PED grows by w_l tau^2 |r'_l - t_l|^2.
 // The zero perturbation is candidate 0; the warp's (PED, index) minimum wins
 // (ties: lower index). w = P u with u = s + tau l, gamma = ||w||^2 and x = the
@@ -245,8 +246,8 @@ __host__ __device__ constexpr int ct_size(int KT) { return ct_off(KT); }   // fl
 // Fills the block's column table from U~ as (re, im, im, re)-packed float4
 // [K][K] (level order): one pass over U~, a thread per entry above the
 // diagonal writing its nine codes, then the points -t at m = lv. Only those
-// entries are ever read (valid codes, m <= lv < K). FIX rounds the entries of U~ to words first, so a table
-// entry (the sum of two words) is exact.
+// entries are ever read (valid codes, m <= lv < K). FIX rounds the entries of
+// U~ to words first, so a table entry (the sum of two words) is exact.
 template <bool FIX>
 __device__ void build_ctab(float2* ctab, const float4* utp_g, int K, const FixP& fx)
 {
