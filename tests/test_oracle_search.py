@@ -235,3 +235,109 @@ def test_bad_channels_give_zero_outputs(orc):
     out = run_batch(orc, H, sym, 16, 16, 2)
     assert out["status"].tolist() == [0, 2, 1]
     assert np.all(out["x"][2:] == 0) and np.all(out["gamma"][2:] == 0)
+
+
+# --------------------------------------------------------------------------
+# The path digit of level l drives level l. Eq. (mop) scores digit p_l with
+# the weight |Rt_ll|^2 of level l, and DEMAP in Alg. 2 applies that same digit
+# at level l. The tests below rebuild every candidate in numpy from those
+# definitions, at budgets 1 < n < 9^K, where the binding decides the result.
+
+def numpy_candidates(U, v, tau, codes):
+    """t and d = ||U (v - tau t)||^2 of the zero candidate and every path, level
+    by level from level K: effective point of Eq. (17) on numpy's factor U,
+    DEMAP = the digit-th entry of the 9 points sorted by (squared distance,
+    alphabet index), the digit taken from nibble l of the code."""
+    K = U.shape[0]
+    pts = np.array([complex(a // 3 - 1, a % 3 - 1) for a in range(9)])
+    ts = [np.zeros(K, dtype=complex)]
+    for code in codes:
+        t = np.zeros(K, dtype=complex)
+        for l in range(K - 1, -1, -1):
+            s_hat = (U[l, l:] @ v[l:] - tau * (U[l, l + 1:] @ t[l + 1:])) / (U[l, l] * tau)
+            dist = np.abs(s_hat - pts) ** 2
+            order = np.lexsort((np.arange(9), dist))
+            t[l] = pts[order[(int(code) >> (4 * l)) & 15]]
+        ts.append(t)
+    return ts, np.array([gamma_np(U, v, tau, t) for t in ts])
+
+
+@pytest.mark.parametrize("K,M,qam,n", [(3, 3, 16, 50), (3, 4, 64, 200), (4, 4, 16, 16), (4, 4, 16, 300)])
+def test_digit_of_level_l_drives_level_l(orc, K, M, qam, n):
+    rng = np.random.default_rng(7000 + 10 * K + n)
+    tau = orc.default_tau(qam)
+    for _ in range(6):
+        H, f, ul, s_user, v = setup_problem(orc, rng, K, M, qam)
+        U = numpy_factor(H, ul)
+        w = np.abs(np.diag(U)) ** 2
+        codes, met = orc.mop_kbest(f["w"], n)
+        # Eq. (mop): nibble l of a code is scored by the weight of level l
+        nib = np.array([[(int(c) >> (4 * l)) & 15 for l in range(K)] for c in codes])
+        assert np.allclose(nib @ w, met, rtol=1e-9, atol=1e-12)
+        # Alg. 2: the same nibble picks the DEMAP rank at level l
+        ts, d = numpy_candidates(U, v, tau, codes)
+        r = orc.search_vector(f["Rt"], f["Qbar"], M, v, tau, codes, want_all=True)
+        assert np.allclose(r["d"], d, rtol=1e-9)
+        kb = int(np.argmin(d))
+        assert r["best"] == kb and np.allclose(r["t"], ts[kb])
+
+
+@pytest.mark.parametrize("K,M,qam,n", [(3, 3, 16, 50), (4, 4, 16, 16)])
+def test_pipeline_and_fixed_search_bind_digits_to_levels(orc, K, M, qam, n):
+    """The batch pipeline, in floating point and as the fixed-point search with
+    53-bit words (no rounding that matters), picks the numpy-built argmin."""
+    rng = W.rng_for(96, 10 * K + n)
+    C, S = 4, 5
+    H = W.channels(rng, C, K, M)
+    sym = W.symbols(rng, C * S, K, qam)
+    tau = orc.default_tau(qam)
+    outs = [run_batch(orc, H, sym, qam, n, S),
+            orc.precode_batch(H, sym, W.vec_offsets_uniform(C, S), qam, n, frac_bits=40, word_bits=53)]
+    for c in range(C):
+        f = orc.factor_channel(H[c], n)
+        ul = f["user_of_level"]
+        U = numpy_factor(H[c].astype(np.complex128), ul)
+        for k in range(S):
+            vi = c * S + k
+            v = orc.qam_points(qam, sym[vi])[ul]
+            ts, d = numpy_candidates(U, v, tau, f["codes"])
+            kb = int(np.argmin(d))
+            for out in outs:
+                # the chosen candidate is the minimum; an exact tie (the zero
+                # candidate against an all-zero path) may go either way, by the
+                # order of the sums
+                kc = int(out["best"][vi])
+                assert kc == kb or np.isclose(d[kc], d[kb], rtol=1e-13, atol=0)
+                assert np.isclose(out["gamma"][vi], d[kb], rtol=1e-9)
+                lv = out["l"][vi, :, 0] + 1j * out["l"][vi, :, 1]
+                assert np.allclose(lv[ul], -ts[kc])
+
+
+GOLD_SEARCH = os.path.join(os.path.dirname(__file__), "golden", "search_k2.txt")
+
+
+def read_search_gold():
+    cases = []
+    for line in open(GOLD_SEARCH):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = dict(kv.split("=", 1) for kv in line.split(";"))
+        Rt = np.array([complex(s) for s in f["Rt"].split()]).reshape(2, 2)
+        v = np.array([complex(s) for s in f["v"].split()])
+        codes = np.array([int(s) for s in f["codes"].split()], dtype=np.uint64)
+        d = np.array([float(s) for s in f["d"].split()])
+        t = np.array([complex(s) for s in f["t"].split()])
+        cases.append((Rt, v, float(f["tau"]), codes, d, int(f["best"]), t))
+    return cases
+
+
+@pytest.mark.parametrize("case", read_search_gold())
+def test_search_golden_two_levels(orc, case):
+    Rt, v, tau, codes, d, best, t = case
+    w = np.abs(np.diag(Rt)) ** 2
+    got_codes, _ = orc.mop_kbest(w, len(codes))
+    assert got_codes.tolist() == codes.tolist()
+    r = orc.search_vector(Rt, np.eye(2), 2, v, tau, codes, want_all=True)
+    assert np.allclose(r["d"], d, rtol=1e-12)
+    assert r["best"] == best and np.allclose(r["t"], t)
