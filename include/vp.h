@@ -74,7 +74,10 @@ typedef enum {
 #define VP_MAX_PATHS 1024
 
 /*
- * Create a plan for one problem shape.
+ * Create a plan for one problem shape: the inputs of Alg. 2 other than the
+ * channel and the symbols (the user count N_R = K, the antenna count N_T = M,
+ * the QAM order of the symbols v, the number of most promising perturbation
+ * vectors, and the perturbation interval tau of Section II-B).
  *   K        users, 1 <= K <= VP_MAX_K
  *   M        antennas, 1 <= M <= VP_MAX_M; K > M (overloaded) needs lambda > 0
  *            (vp_plan_set_lambda) before vp_factorize
@@ -169,7 +172,13 @@ vp_status vp_factorize(vp_plan* plan, const void* H, int C, void* U, void* P,
                        uint8_t* user_of_level, uint8_t* status, void* stream);
 
 /*
- * Precode data vectors against the channels of the last vp_factorize.
+ * Precode data vectors against the channels of the last vp_factorize: Alg. 2
+ * "Parallel post-processing". For each vector every candidate path descends
+ * the levels from level K; at level l the DEMAP point is the p_l-th nearest
+ * of the bounded alphabet to the effective point of Eq. (17), the partial
+ * distance grows as in the PED recursion of Section II-B, and the candidate
+ * with the smallest d^(k) = ||w^(k)||^2 gives x = w^(k*) / sqrt(d^(k*))
+ * (Eqs. 24-25 with P_T = 1). The zero perturbation competes as candidate 0.
  *   sym_idx      uint8 [V][K], QAM indices in USER order
  *   S            vectors per channel when vec_offsets is NULL (V = C*S,
  *                vector v belongs to channel v / S)
@@ -220,15 +229,16 @@ vp_status vp_run_slot_host(vp_plan* plan, const void* H_host, int C, const uint8
  * another framework's allocator; hosts that only hand this library device
  * buffers. The per-channel state that a plan keeps
  * in cudaMalloc'd memory lives instead in one static device array of
- * vp_noalloc_capacity_bytes() bytes (8 MiB, e.g. 640 channels at K = M = 16
- * with 256 paths); every GPU that loads the library holds that array until
- * the process exits.
+ * vp_noalloc_capacity_bytes() bytes (8 MiB); vp_noalloc_max_channels(plan)
+ * gives the largest C that fits for the plan's shape. Every GPU that loads
+ * the library holds that array until the process exits.
  *   plan     supplies the parameters only (K, M, qam, n_paths, tau, FP64
  *            threshold); its own device state is neither used nor allocated
  *   H        complex64 [C][K][M]; sym_idx uint8 [C*S][K] (vector v -> channel v / S)
  *   x, l, gamma  as vp_precode; status optional uint8 [C] as vp_factorize
- * Returns VP_ERR_CAPACITY when C channels of this shape do not fit, with
- * nothing enqueued. The first call on a device looks up the array's device
+ * Returns VP_ERR_CAPACITY when C channels of this shape do not fit
+ * (C > vp_noalloc_max_channels(plan)), and VP_ERR_INVALID_ARG when C * S
+ * exceeds INT_MAX, with nothing enqueued. The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture. All calls share the one array, which keeps
  * the last call's contents: calls whose work overlaps on the GPU (different
@@ -239,6 +249,12 @@ vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const ui
 
 /* Size in bytes of the static device array behind vp_precode_noalloc. */
 size_t vp_noalloc_capacity_bytes(void);
+
+/* Largest channel count C that vp_precode_noalloc accepts for the plan's
+ * shape (K, M, n_paths, lambda): the per-channel state of C channels, each
+ * piece 256-byte aligned, fits vp_noalloc_capacity_bytes(). Host only; 0 for
+ * a null plan. */
+int vp_noalloc_max_channels(const vp_plan* plan);
 
 /*
  * Uneven batches: many independent problems of different shape in a few

@@ -24,7 +24,7 @@ __all__ = [
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
     "vp_plan_set_fixed_point", "vp_plan_destroy", "vp_factorize", "vp_precode", "vp_get_paths", "vp_run_slot_host",
     "vp_last_launch_count", "vp_status_string",
-    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_problem_desc", "vp_batch_create", "VP_DEMAP_EXACT", "VP_DEMAP_LUT",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_noalloc_max_channels", "vp_problem_desc", "vp_batch_create", "VP_DEMAP_EXACT", "VP_DEMAP_LUT",
     "vp_batch_workspace_bytes", "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy",
     "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
     "vp_job_desc", "vp_job_done", "vp_server_stats", "vp_server_create", "vp_server_submit", "vp_server_poll",
@@ -49,7 +49,8 @@ EXPORTED_SYMBOLS = (
     "vp_factorize",
     "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
-    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_batch_create", "vp_batch_workspace_bytes",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_noalloc_max_channels", "vp_batch_create",
+    "vp_batch_workspace_bytes",
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
     "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "vp_batch_autotune", "vp_batch_get_tuning",
@@ -129,6 +130,8 @@ def load():
             L.vp_precode_noalloc.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp, vpp]
             L.vp_noalloc_capacity_bytes.argtypes = []
             L.vp_noalloc_capacity_bytes.restype = ctypes.c_size_t
+            L.vp_noalloc_max_channels.argtypes = [vpp]
+            L.vp_noalloc_max_channels.restype = ctypes.c_int
             descp = ctypes.POINTER(vp_problem_desc)
             L.vp_batch_create.argtypes = [descp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(vpp)]
             L.vp_batch_workspace_bytes.argtypes = [vpp]
@@ -265,6 +268,11 @@ def vp_precode_noalloc(plan: int, H, C: int, sym_idx, S: int, x, l, gamma, statu
 
 def vp_noalloc_capacity_bytes() -> int:
     return int(load().vp_noalloc_capacity_bytes())
+
+
+def vp_noalloc_max_channels(plan: int) -> int:
+    """Largest channel count vp_precode_noalloc accepts for the plan's shape."""
+    return int(load().vp_noalloc_max_channels(plan))
 
 
 def vp_last_launch_count(plan: int) -> int:

@@ -100,10 +100,31 @@ extern "C" {
 
 size_t vp_noalloc_capacity_bytes(void) { return kNoAllocBytes; }
 
+int vp_noalloc_max_channels(const vp_plan* plan)
+{
+    if (!plan) return 0;
+    const int mp = vp::p_rows(plan);
+    vp::DeviceState probe;
+    // the state grows with C, so the largest fitting C is found by bisection
+    int lo = 0, hi = 1;
+    while (vp::carve_state(nullptr, hi, plan->K, mp, plan->n_paths, &probe) <= kNoAllocBytes) {
+        lo = hi;
+        if (hi > (1 << 28)) return lo;
+        hi *= 2;
+    }
+    while (hi - lo > 1) {
+        const int mid = lo + (hi - lo) / 2;
+        if (vp::carve_state(nullptr, mid, plan->K, mp, plan->n_paths, &probe) <= kNoAllocBytes) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 vp_status vp_precode_noalloc(const vp_plan* plan, const void* H, int C, const uint8_t* sym_idx, int S, void* x,
                              int8_t* l, float* gamma, uint8_t* status, void* stream)
 {
     if (!plan || !H || !sym_idx || !x || !l || !gamma || C < 1 || S < 0) return VP_ERR_INVALID_ARG;
+    if ((long long)C * S > 0x7fffffffLL) return VP_ERR_INVALID_ARG;
     if (plan->K > plan->M && !(plan->lambda > 0.f)) return VP_ERR_INVALID_ARG;
     const int mp = vp::p_rows(plan);
     vp::DeviceState probe;

@@ -6,6 +6,8 @@ call runs on storage the first one left behind. Outputs must agree within the
 parity tolerances of the other GPU tests (the kernels are the same, so they
 are expected to agree exactly). Kept in a file of its own, collected last.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -82,19 +84,26 @@ def test_noalloc_matches_plan_path_two_calls():
         _assert_close(out, ref)
 
 
-def test_noalloc_rejects_oversized_batch():
+def test_noalloc_capacity_boundary():
+    """The largest channel count the library reports is accepted and matches the
+    plan path; one more channel is refused with VP_ERR_CAPACITY."""
     wl = W.SLOT_16x16
     K, M = wl.K, wl.M
-    per_channel = 16 * K * K + 8 * K * K + 4 * K + K + 16 * K * M + 8 * wl.n_paths
-    C = vp.vp_noalloc_capacity_bytes() // per_channel + 1
-    dev = torch.device("cuda:0")
-    H = torch.zeros((C, K, M), dtype=torch.complex64, device=dev)
-    sym = torch.zeros((C, K), dtype=torch.uint8, device=dev)
-    x = torch.zeros((C, M), dtype=torch.complex64, device=dev)
-    l = torch.zeros((C, K, 2), dtype=torch.int8, device=dev)
-    g = torch.zeros((C,), dtype=torch.float32, device=dev)
+    S = 2
     with vp.Plan(K, M, wl.qam, wl.n_paths) as plan:
+        cmax = vp.vp_noalloc_max_channels(plan.handle)
+        assert 0 < cmax < 100000
+        b = W.make_batch(dataclasses.replace(wl, symbols=S), slot=5, subcarriers=cmax)
+        out = _noalloc(plan, b, S)
+        dev = torch.device("cuda:0")
+        C = cmax + 1
+        H = torch.zeros((C, K, M), dtype=torch.complex64, device=dev)
+        sym = torch.zeros((C, K), dtype=torch.uint8, device=dev)
+        x = torch.zeros((C, M), dtype=torch.complex64, device=dev)
+        l = torch.zeros((C, K, 2), dtype=torch.int8, device=dev)
+        g = torch.zeros((C,), dtype=torch.float32, device=dev)
         with pytest.raises(vp.VPError) as e:
             vp.vp_precode_noalloc(plan.handle, H, C, sym, 1, x, l, g)
-    assert e.value.code == 6
-    torch.cuda.synchronize()
+        assert e.value.code == 6
+        torch.cuda.synchronize()
+    _assert_close(out, _plan_path(b, S))
