@@ -148,6 +148,23 @@ vp_status vp_plan_set_demap(vp_plan* plan, int demap);
  */
 vp_status vp_plan_set_fixed_point(vp_plan* plan, int frac_bits);
 
+/*
+ * Where vp_precode forms the output w = P u (Eqs. 24-25, the PV block of
+ * Section IV-B; P = H^H (H H^H)^-1, u = s + tau l, exact small integers):
+ *   0  CUDA cores (the default): exact products and compensated sums, per
+ *      data vector;
+ *   1  tensor cores: per channel and round of 16 data vectors, one TF32
+ *      matrix product (mma.sync m16n8k8) of the real form [[Re P, -Im P],
+ *      [Im P, Re P]] with P split into three 11-bit pieces on per-row grids,
+ *      so that every product and partial sum is exact, then one error-free
+ *      addition of the three (P kept to 2^-33 of its row's largest entry).
+ * Both agree to FP32 rounding; the search and l are the same. Applies to
+ * the exact floating-point search (not the region LUT or fixed-point
+ * variants, which use the CUDA-core form). Takes effect at the next
+ * vp_precode. Other values are invalid.
+ */
+vp_status vp_plan_set_tensor_product(vp_plan* plan, int enable);
+
 /* Free the plan and its device state. Synchronises the device first so that
  * no enqueued work still reads the state. NULL is accepted. */
 vp_status vp_plan_destroy(vp_plan* plan);

@@ -24,7 +24,8 @@ __all__ = [
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
     "vp_plan_set_fixed_point", "vp_plan_destroy", "vp_factorize", "vp_precode", "vp_get_paths", "vp_run_slot_host",
     "vp_last_launch_count", "vp_status_string",
-    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_noalloc_max_channels", "vp_problem_desc", "vp_batch_create", "VP_DEMAP_EXACT", "VP_DEMAP_LUT",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_noalloc_max_channels", "vp_problem_desc",
+    "vp_plan_set_tensor_product", "vp_batch_create", "VP_DEMAP_EXACT", "VP_DEMAP_LUT",
     "vp_batch_workspace_bytes", "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy",
     "vp_precode_batch", "vp_precode_batch_workspace_bytes", "problem_desc", "packed_descs", "Batch", "VP_CH_NONFINITE", "VP_CH_SINGULAR", "VP_CH_FP64", "VP_MAX_K", "VP_MAX_M", "VP_MAX_PATHS",
     "vp_job_desc", "vp_job_done", "vp_server_stats", "vp_server_create", "vp_server_submit", "vp_server_poll",
@@ -49,7 +50,8 @@ EXPORTED_SYMBOLS = (
     "vp_factorize",
     "vp_precode",
     "vp_get_paths", "vp_run_slot_host", "vp_last_launch_count", "vp_status_string",
-    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_noalloc_max_channels", "vp_batch_create",
+    "vp_precode_noalloc", "vp_noalloc_capacity_bytes", "vp_noalloc_max_channels", "vp_plan_set_tensor_product",
+    "vp_batch_create",
     "vp_batch_workspace_bytes",
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
@@ -120,6 +122,7 @@ def load():
             L.vp_plan_set_lambda.argtypes = [vpp, ctypes.c_float]
             L.vp_plan_set_demap.argtypes = [vpp, ctypes.c_int]
             L.vp_plan_set_fixed_point.argtypes = [vpp, ctypes.c_int]
+            L.vp_plan_set_tensor_product.argtypes = [vpp, ctypes.c_int]
             L.vp_plan_destroy.argtypes = [vpp]
             L.vp_factorize.argtypes = [vpp, vpp, ctypes.c_int, vpp, vpp, vpp, vpp, vpp]
             L.vp_precode.argtypes = [vpp, vpp, ctypes.c_int, vpp, ctypes.c_int, vpp, vpp, vpp, vpp]
@@ -169,7 +172,7 @@ def load():
             L.vp_status_string.argtypes = [ctypes.c_int]
             L.vp_status_string.restype = ctypes.c_char_p
             for name in ("vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
-                         "vp_plan_set_fixed_point", "vp_plan_destroy",
+                         "vp_plan_set_fixed_point", "vp_plan_set_tensor_product", "vp_plan_destroy",
                          "vp_factorize",
                          "vp_precode", "vp_get_paths", "vp_run_slot_host", "vp_precode_noalloc", "vp_batch_create",
                          "vp_batch_bind", "vp_batch_launch", "vp_batch_destroy", "vp_precode_batch"):
@@ -234,6 +237,10 @@ def vp_plan_set_demap(plan: int, demap: int) -> None:
 
 def vp_plan_set_fixed_point(plan: int, frac_bits: int) -> None:
     _check(load().vp_plan_set_fixed_point(plan, int(frac_bits)), "vp_plan_set_fixed_point")
+
+
+def vp_plan_set_tensor_product(plan: int, enable: int) -> None:
+    _check(load().vp_plan_set_tensor_product(plan, int(enable)), "vp_plan_set_tensor_product")
 
 
 def vp_plan_destroy(plan: int) -> None:
@@ -546,7 +553,8 @@ class Plan:
     """Owning handle of a vp_plan (destroys it on close / exit of a with-block)."""
 
     def __init__(self, K: int, M: int, qam: int, n_paths: int, tau: float = 0.0,
-                 fp64_threshold: float | None = None, lam: float = 0.0, demap: int = 0, frac_bits: int = 0):
+                 fp64_threshold: float | None = None, lam: float = 0.0, demap: int = 0, frac_bits: int = 0,
+                 tensor_product: int = 0):
         self.K, self.M, self.qam, self.n_paths = K, M, qam, n_paths
         self.handle = vp_plan_create(K, M, qam, n_paths, tau)
         if fp64_threshold is not None:
@@ -557,6 +565,8 @@ class Plan:
             vp_plan_set_demap(self.handle, demap)
         if frac_bits:
             vp_plan_set_fixed_point(self.handle, frac_bits)
+        if tensor_product:
+            vp_plan_set_tensor_product(self.handle, tensor_product)
 
     def close(self):
         if self.handle:

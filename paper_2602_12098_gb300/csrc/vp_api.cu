@@ -194,6 +194,13 @@ vp_status vp_plan_set_fixed_point(vp_plan* p, int frac_bits)
     return VP_OK;
 }
 
+vp_status vp_plan_set_tensor_product(vp_plan* p, int enable)
+{
+    if (!p || (enable != 0 && enable != 1)) return VP_ERR_INVALID_ARG;
+    p->tensor_product = enable;
+    return VP_OK;
+}
+
 vp_status vp_plan_destroy(vp_plan* p)
 {
     if (!p) return VP_OK;

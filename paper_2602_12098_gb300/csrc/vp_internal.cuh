@@ -144,6 +144,7 @@ struct vp_plan {
     float lambda = 0.f;   // Tikhonov parameter (Hbar = [H lambda*I])
     int demap = VP_DEMAP_EXACT;
     int frac_bits = 0;                  // fixed-point search with 16-bit words (0 = floating point)
+    int tensor_product = 0;             // w = P u on the tensor cores (vp_plan_set_tensor_product)
     int cap = 0;   // channel capacity of `d`
     int cap_mp = 0;  // rows of P that `d` was allocated for
     int C = 0;     // channels of the last vp_factorize

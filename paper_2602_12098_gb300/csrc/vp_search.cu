@@ -53,6 +53,7 @@ struct SearchArgs {
     int KM, NP;
     int demap;       // VP_DEMAP_* (plan launches)
     int frac;        // fractional bits of the fixed-point search (0: floating point)
+    int tcp;         // 1: w = P u on the tensor cores (plan launches, exact DEMAP, floating point)
 };
 
 // One level of the descent for a lane's candidate: DEMAP selection of the
@@ -136,6 +137,150 @@ __device__ __forceinline__ void pair_rows_out(const float2* pt, const float2* pt
     __syncwarp(kFull);
 }
 
+// ---------------------------------------------------------------------------
+// w = P u on the tensor cores (Eqs. 24-25, the PV block of Section IV-B), for
+// a round of up to kTcCols data vectors of one channel, by the whole block.
+//
+// In real form W = A V with A = [[Re P, -Im P], [Im P, Re P]] (2Mp x 2K, user
+// order) and V = [Re u; Im u] (2K x vectors). u holds small integers
+// (|Re u|, |Im u| <= 47), exact in TF32. P = ph + pl is split, per complex
+// row m, into three pieces on the grids 2^(E_m - 10), 2^(E_m - 21) and
+// 2^(E_m - 32), where 2^E_m bounds the row's largest component (the
+// error-free splitting of Ozaki et al. for exact matrix products): each piece
+// is an integer of at most 11 bits times its grid, exact in TF32, so every
+// product is exact, and every partial sum of a piece's product (at most 32
+// terms of at most 2^16 grid units) stays below 2^22 grid units, so the FP32
+// accumulation of the tensor cores is exact as well. The three exact piece
+// products are added by one error-free addition; the split keeps P to 2^-33
+// of its row's largest entry, below the FP32 rounding of P itself.
+// mma.sync m16n8k8 (TF32 in, FP32 accumulate): a warp per 16 x 8 output
+// tile. The pieces are staged row-major in shared memory with row stride
+// 2K + 4 floats (the 8 rows x 4 columns a fragment reads fall on distinct
+// banks), V as [2K][24] floats (conflict-free for the B fragment).
+constexpr int kTcCols = 16;     // vectors per round
+constexpr int kTcVs = 24;       // row stride of V and W (floats)
+
+__host__ __device__ inline int tc_pad16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int tc_pad8(int x) { return (x + 7) & ~7; }
+
+// Bytes of the round's work area (pieces, V, W, row exponents).
+__host__ __device__ inline int tc_area_bytes(int K, int Mp)
+{
+    const int mp2 = tc_pad16(2 * Mp), k2 = tc_pad8(2 * K);
+    return 4 * (3 * mp2 * (k2 + 4) + k2 * kTcVs + mp2 * kTcVs + 32);
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One round: vectors v0r .. v0r + nv - 1 of the channel, their u (level
+// order) in ust[col][level]. Every thread of the block calls it, after the
+// round's searches. Writes x (antenna rows of w / sqrt(gamma)) and gamma.
+__device__ void tc_round(const float2* __restrict__ pt, const float2* __restrict__ ptl, const int* ulv,
+                         const float2* ust, int KT, int K, int M, int Mp, int v0r, int nv, float* area, float2* xo,
+                         float* go)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, NW = nthr >> 5;
+    const int mp2 = tc_pad16(2 * Mp), k2 = tc_pad8(2 * K), as = k2 + 4;
+    float* Ap = area;                                  // [3][mp2][as]
+    float* V = Ap + 3 * mp2 * as;                      // [k2][kTcVs]
+    float* W = V + k2 * kTcVs;                         // [mp2][kTcVs]
+    int* Es = reinterpret_cast<int*>(W + mp2 * kTcVs); // [Mp] row exponents
+    __syncthreads();                                   // the round's searches are done; area is free
+    for (int m = tid; m < Mp; m += nthr) {
+        float mx = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const float2 z = pt[k * Mp + m];
+            mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.y)));
+        }
+        int e = 0;
+        frexpf(mx, &e);                                // mx < 2^e
+        Es[m] = e;
+    }
+    for (int i = tid; i < k2 * kTcCols; i += nthr) {   // V: Re u over the users, then Im u
+        const int kr = i / kTcCols, col = i - kr * kTcCols;
+        float v = 0.f;
+        if (col < nv && kr < 2 * K) {
+            const int usr = kr < K ? kr : kr - K;
+            int lev = 0;
+            for (int l = 0; l < K; ++l) lev = ulv[l] == usr ? l : lev;
+            const float2 u = ust[col * KT + lev];
+            v = kr < K ? u.x : u.y;
+        }
+        V[kr * kTcVs + col] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < mp2 * k2; i += nthr) {       // the three pieces of A
+        const int R = i / k2, C = i - R * k2;
+        float p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        if (R < 2 * Mp && C < 2 * K) {
+            const int pr = R >= Mp, m = R - pr * Mp, pc = C >= K, k = C - pc * K;
+            const float2 zh = pt[k * Mp + m], zl = ptl[k * Mp + m];
+            float vh, vl;                               // [[Re, -Im], [Im, Re]]
+            if (pr == pc) { vh = zh.x; vl = zl.x; }
+            else if (pc) { vh = -zh.y; vl = -zl.y; }
+            else { vh = zh.y; vl = zl.y; }
+            const int E = Es[m];
+            const float t = ldexpf(vh, 10 - E);        // |t| < 2^10, exact scaling
+            p1 = rintf(t);
+            float r = __fadd_rn(__fsub_rn(t, p1), ldexpf(vl, 10 - E)) * 2048.f;
+            p2 = rintf(r);
+            r = __fsub_rn(r, p2) * 2048.f;
+            p3 = rintf(r);
+        }
+        Ap[R * as + C] = p1;
+        Ap[mp2 * as + R * as + C] = p2;
+        Ap[2 * mp2 * as + R * as + C] = p3;
+    }
+    __syncthreads();
+    const int g = lane >> 2, t4 = lane & 3;
+    const int ntile = nv > 8 ? 2 : 1, ntiles = (mp2 >> 4) * ntile;
+    for (int tile = warp; tile < ntiles; tile += NW) {
+        const int mt = tile / ntile, nt = tile - mt * ntile;
+        float acc[3][4] = {};
+        for (int ks = 0; ks < (k2 >> 3); ++ks) {
+            const uint32_t b0 = __float_as_uint(V[(8 * ks + t4) * kTcVs + 8 * nt + g]);
+            const uint32_t b1 = __float_as_uint(V[(8 * ks + t4 + 4) * kTcVs + 8 * nt + g]);
+#pragma unroll
+            for (int pc = 0; pc < 3; ++pc) {
+                const float* A = Ap + pc * mp2 * as + (16 * mt + g) * as + 8 * ks + t4;
+                mma_tf32(acc[pc], __float_as_uint(A[0]), __float_as_uint(A[8 * as]), __float_as_uint(A[4]),
+                         __float_as_uint(A[8 * as + 4]), b0, b1);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {                   // c0..c3: rows g, g, g+8, g+8; columns 2 t4, 2 t4 + 1
+            const int R = 16 * mt + g + (e >> 1) * 8, col = 8 * nt + 2 * t4 + (e & 1);
+            if (R < 2 * Mp) {
+                const int m = R >= Mp ? R - Mp : R, E = Es[m];
+                const float x1 = ldexpf(acc[0][e], E - 10), x2 = ldexpf(acc[1][e], E - 21), x3 = ldexpf(acc[2][e], E - 32);
+                float sh, sl;
+                two_sum(x1, x2, sh, sl);
+                W[R * kTcVs + col] = __fadd_rn(sh, __fadd_rn(sl, x3));
+            }
+        }
+    }
+    __syncthreads();
+    for (int col = warp; col < nv; col += NW) {         // gamma = ||w||^2 over all rows, x = antenna rows / sqrt
+        float gsum = 0.f;
+        for (int R = lane; R < 2 * Mp; R += 32) gsum += W[R * kTcVs + col] * W[R * kTcVs + col];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+        const float rs = __frsqrt_rn(gsum);
+        const int v = v0r + col;
+        if (lane < M) xo[(size_t)v * M + lane] = make_float2(W[lane * kTcVs + col] * rs, W[(lane + Mp) * kTcVs + col] * rs);
+        if (lane == 0) go[v] = gsum;
+    }
+    __syncthreads();                                   // the area and ust are reused by the next round
+}
+
 __host__ __device__ inline int take16(int& o, int bytes)
 {
     const int r = o;
@@ -152,19 +297,23 @@ __host__ __device__ inline int take16(int& o, int bytes)
 constexpr int kSearchSmemBudget = 57344;   // (228 KB per SM) / 4 - 1 KB reserved per block
 
 struct SearchSmem {
-    int ctab, utc, pt, ptl, bvec, scr, tmq, pcode, lut, scrl, scrp, wv, ulv, tc, meta, total;
+    int ctab, utc, pt, ptl, ust, bvec, scr, tmq, pcode, lut, scrl, scrp, wv, ulv, tc, meta, total;
 };
 
-__host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW, bool gp)
+// tcp: the tensor-core product (u of a round staged in ust; the prefix-state
+// area scr doubles as its work area after each round, sized for MPL rows of
+// P), else the CUDA-core one (P staged in pt / ptl).
+__host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW, bool gp, bool tcp = false, int MPL = 0)
 {
     SearchSmem s;
     int o = 0;
     s.ctab = take16(o, 8 * ct_size(KT));
     s.utc = take16(o, 8 * KT * KT);
-    s.pt = take16(o, 8 * KM);
-    s.ptl = take16(o, 8 * KM);
+    s.pt = tcp ? -1 : take16(o, 8 * KM);
+    s.ptl = tcp ? -1 : take16(o, 8 * KM);
+    s.ust = tcp ? take16(o, 8 * kTcCols * KT) : -1;
     s.bvec = take16(o, 8 * NW * KT);
-    s.scr = take16(o, 8 * NW * KT * kMaxPrefix);
+    s.scr = take16(o, tcp ? max(8 * NW * KT * kMaxPrefix, tc_area_bytes(KT, MPL)) : 8 * NW * KT * kMaxPrefix);
     s.tc = gp ? -1 : take16(o, 8 * NP);
     s.tmq = take16(o, 8 * n_chunks(NP));
     s.pcode = take16(o, 8 * kMaxPrefix);
@@ -186,7 +335,7 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
 // then continues from its prefix's state through the remaining levels. The
 // arithmetic per path is the same as a full descent, so results are
 // identical; the shared levels are the ones with the most column updates.
-template <int KT, bool BATCH, bool LUT, bool FIX, bool GP>
+template <int KT, bool BATCH, bool LUT, bool FIX, bool GP, bool TC>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -222,11 +371,12 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         sym = a.sym; xo = a.x; lo = a.l; go = a.gamma;
     }
     const int KM = BATCH ? a.KM : K * Mp, NP = BATCH ? a.NP : n;
-    const SearchSmem L = search_smem(KT, KM, NP, NW, GP);
+    const SearchSmem L = search_smem(KT, KM, NP, NW, GP, TC, Mp);
     float2* ctab = reinterpret_cast<float2*>(smraw + L.ctab);      // column table
     float2* utc = reinterpret_cast<float2*>(smraw + L.utc);        // [KT][KT]
-    float2* pt = reinterpret_cast<float2*>(smraw + L.pt);          // [K][M] leading part of P^T
-    float2* ptl = reinterpret_cast<float2*>(smraw + L.ptl);        // [K][M] trailing part
+    float2* pt = TC ? nullptr : reinterpret_cast<float2*>(smraw + L.pt);     // [K][M] leading part of P^T
+    float2* ptl = TC ? nullptr : reinterpret_cast<float2*>(smraw + L.ptl);   // [K][M] trailing part
+    float2* ust = TC ? reinterpret_cast<float2*>(smraw + L.ust) : nullptr;   // [kTcCols][KT] u of a round
     float2* bvec = reinterpret_cast<float2*>(smraw + L.bvec);      // [NW][KT]
     float2* scr_all = reinterpret_cast<float2*>(smraw + L.scr);    // [NW][KT][32] prefix residuals
     // [n] codes in evaluation order and their MoP rank | prefix << 16 (staged unless GP)
@@ -262,9 +412,11 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
         utc[i] = uc;
     }
     build_ctab<FIX>(ctab, cs.utp, K, fx);
-    for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
-        pt[i] = cs.pt[i];
-        ptl[i] = cs.ptlo[i];
+    if (!TC) {
+        for (int i = threadIdx.x; i < K * Mp; i += blockDim.x) {
+            pt[i] = cs.pt[i];
+            ptl[i] = cs.ptlo[i];
+        }
     }
     // evaluation order, shared prefixes and chunk digit maxima (from path selection)
     if (!GP) {
@@ -292,16 +444,10 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
     float* scrp = scrp_all + warp * kMaxPrefix;
     uint2* scrl = scrl_all + warp * kMaxPrefix;
     const int KB = K - T;   // levels evaluated per path
-    // The warp takes its vectors in pairs (v, v + NW): both are searched in
-    // turn, then one pass forms y = P u for both, one half-warp each (when the
-    // Mp rows fit 16 lanes; else each vector gets a whole-warp pass).
-    const bool pair_rows = Mp <= 16;
-    for (int v = v0 + warp; v < v1; v += 2 * NW) {
-        float2 upk = make_float2(0.f, 0.f);   // u of the pair: lanes 0-15 levels of v, lanes 16-31 of v + NW
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int vh = v + h * NW;
-            if (vh >= v1) break;
+    // One data vector on the warp: b', the shared prefixes, every path, the
+    // (PED, rank) argmin against the zero candidate; writes l and returns u =
+    // s + tau l in level order (lane k <-> level k, lanes >= K zero).
+    auto search_vec = [&](int vh) -> float2 {
             // symbols in level order (lane k <-> level k) and b_k = s_k + sum_{m>k} U~_km s_m
             float2 s = make_float2(0.f, 0.f);
             if (lane < K) s = qam_point((int)sym[(size_t)vh * K + ulv[lane]], m_qam);
@@ -396,28 +542,58 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
                 lo[((size_t)vh * K + usr) * 2] = (int8_t)(-tr);
                 lo[((size_t)vh * K + usr) * 2 + 1] = (int8_t)(-ti);
             }
-            if (pair_rows) {
-                const float ux = __shfl_sync(kFull, u.x, lane & 15), uy = __shfl_sync(kFull, u.y, lane & 15);
-                if ((lane >> 4) == h) upk = make_float2(ux, uy);
+            return u;
+    };
+
+    if constexpr (TC) {
+        // rounds of kTcCols vectors: the warp searches v, v + NW, ... of the
+        // round, then the block forms w = P u for the round (tc_round)
+        for (int r0 = v0; r0 < v1; r0 += kTcCols) {
+            const int rend = min(r0 + kTcCols, v1);
+#pragma unroll 1
+            for (int vh = r0 + warp; vh < rend; vh += NW) {
+                const float2 u = search_vec(vh);
+                if (lane < KT) ust[(vh - r0) * KT + lane] = u;
                 __syncwarp(kFull);
-                continue;
             }
-            // y = P u with P = pt + ptl, all Mp rows on the warp
-            float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
-            for (int lv = 0; lv < K; ++lv) {
-                const float ur = __shfl_sync(kFull, u.x, lv), ui = __shfl_sync(kFull, u.y, lv);
-                if (lane < Mp) py_acc(pt, ptl, ulv[lv] * Mp + lane, ur, ui, yr, yre, yi, yie);
-            }
-            const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
-            float g = (lane < Mp) ? cabs2(y) : 0.f;     // ||w||^2 over all rows (Alg. 2's d)
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
-            const float rs = __frsqrt_rn(g);
-            if (lane < M) xo[(size_t)vh * M + lane] = make_float2(y.x * rs, y.y * rs);
-            if (lane == 0) go[vh] = g;
-            __syncwarp(kFull);
+            tc_round(cs.pt, cs.ptlo, ulv, ust, KT, K, M, Mp, r0, rend - r0, reinterpret_cast<float*>(smraw + L.scr), xo,
+                     go);
         }
-        if (pair_rows) pair_rows_out(pt, ptl, ulv, upk, K, M, Mp, v, v + NW, v1, xo, go);
+    } else {
+        // The warp takes its vectors in pairs (v, v + NW): both are searched in
+        // turn, then one pass forms y = P u for both, one half-warp each (when
+        // the Mp rows fit 16 lanes; else each vector gets a whole-warp pass).
+        const bool pair_rows = Mp <= 16;
+        for (int v = v0 + warp; v < v1; v += 2 * NW) {
+            float2 upk = make_float2(0.f, 0.f);   // u of the pair: lanes 0-15 levels of v, lanes 16-31 of v + NW
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int vh = v + h * NW;
+                if (vh >= v1) break;
+                const float2 u = search_vec(vh);
+                if (pair_rows) {
+                    const float ux = __shfl_sync(kFull, u.x, lane & 15), uy = __shfl_sync(kFull, u.y, lane & 15);
+                    if ((lane >> 4) == h) upk = make_float2(ux, uy);
+                    __syncwarp(kFull);
+                    continue;
+                }
+                // y = P u with P = pt + ptl, all Mp rows on the warp
+                float yr = 0.f, yre = 0.f, yi = 0.f, yie = 0.f;
+                for (int lv = 0; lv < K; ++lv) {
+                    const float ur = __shfl_sync(kFull, u.x, lv), ui = __shfl_sync(kFull, u.y, lv);
+                    if (lane < Mp) py_acc(pt, ptl, ulv[lv] * Mp + lane, ur, ui, yr, yre, yi, yie);
+                }
+                const float2 y = make_float2(__fadd_rn(yr, yre), __fadd_rn(yi, yie));
+                float g = (lane < Mp) ? cabs2(y) : 0.f;     // ||w||^2 over all rows (Alg. 2's d)
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
+                const float rs = __frsqrt_rn(g);
+                if (lane < M) xo[(size_t)vh * M + lane] = make_float2(y.x * rs, y.y * rs);
+                if (lane == 0) go[vh] = g;
+                __syncwarp(kFull);
+            }
+            if (pair_rows) pair_rows_out(pt, ptl, ulv, upk, K, M, Mp, v, v + NW, v1, xo, go);
+        }
     }
 }
 
@@ -631,13 +807,13 @@ cudaError_t launch_small_kt(const SearchArgs& a, int C, int per, cudaStream_t s)
     return launch_small<KT, 2>(a, C, per, s);
 }
 
-template <int KT, bool BATCH, bool LUT, bool FIX, bool GP>
+template <int KT, bool BATCH, bool LUT, bool FIX, bool GP, bool TC = false>
 cudaError_t launch_one(const SearchArgs& a, int C, int threads, int KM, int NP, cudaStream_t s)
 {
-    const size_t sh = (size_t)search_smem(KT, KM, NP, threads / 32, GP).total;
-    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_kernel<KT, BATCH, LUT, FIX, GP>), sh);
+    const size_t sh = (size_t)search_smem(KT, KM, NP, threads / 32, GP, TC, a.Mp).total;
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_kernel<KT, BATCH, LUT, FIX, GP, TC>), sh);
     if (e != cudaSuccess) return e;
-    search_kernel<KT, BATCH, LUT, FIX, GP><<<C, threads, sh, s>>>(a);
+    search_kernel<KT, BATCH, LUT, FIX, GP, TC><<<C, threads, sh, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -662,6 +838,11 @@ cudaError_t launch_kt(const SearchArgs& a, int C, int threads, cudaStream_t s)
     if (a.probs) return launch_gp<KT, true, false, false>(a, C, threads, KM, NP, s);
     if (a.frac > 0) return launch_gp<KT, false, false, true>(a, C, threads, KM, NP, s);
     if (a.demap == VP_DEMAP_LUT) return launch_gp<KT, false, true, false>(a, C, threads, KM, NP, s);
+    if (a.tcp) {
+        if (search_smem(KT, KM, NP, threads / 32, false, true, a.Mp).total > kSearchSmemBudget)
+            return launch_one<KT, false, false, false, true, true>(a, C, threads, KM, NP, s);
+        return launch_one<KT, false, false, false, false, true>(a, C, threads, KM, NP, s);
+    }
     return launch_gp<KT, false, false, false>(a, C, threads, KM, NP, s);
 }
 
@@ -684,6 +865,7 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     a.Mp = p_rows(p);
     a.demap = p->demap;
     a.frac = p->frac_bits;
+    a.tcp = (p->tensor_product && p->demap == VP_DEMAP_EXACT && p->frac_bits == 0) ? 1 : 0;
     a.n = p->n_paths;
     a.nch = n_chunks(p->n_paths);
     int m = 1;
@@ -705,7 +887,7 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     const int threads = nw * 32;
     const int K = p->K;
     // budgets of 16 paths or fewer: several vectors per warp (same results)
-    if (a.n <= 16 && a.Mp <= 16 && a.demap == VP_DEMAP_EXACT && a.frac == 0 && per >= 2) {
+    if (a.n <= 16 && a.Mp <= 16 && a.demap == VP_DEMAP_EXACT && a.frac == 0 && !a.tcp && per >= 2) {
         if (K <= 2) return launch_small_kt<2>(a, p->C, per, s);
         if (K <= 4) return launch_small_kt<4>(a, p->C, per, s);
         if (K <= 8) return launch_small_kt<8>(a, p->C, per, s);

@@ -19,7 +19,7 @@ X_RTOL = 1e-5
 
 
 def run_gpu(H, sym, vec_off, qam, n, tau=0.0, fp64_threshold=None, want_factor=True, uniform_S=None, lam=0.0,
-            demap=0, frac_bits=0):
+            demap=0, frac_bits=0, tensor_product=0):
     """Whole path on cuda:0 through the C-ABI. Returns numpy outputs."""
     dev = torch.device("cuda:0")
     C, K, M = H.shape
@@ -35,7 +35,8 @@ def run_gpu(H, sym, vec_off, qam, n, tau=0.0, fp64_threshold=None, want_factor=T
     ul = torch.zeros((C, K), dtype=torch.uint8, device=dev) if want_factor else None
     st = torch.zeros((C,), dtype=torch.uint8, device=dev)
     codes = torch.zeros((C, n), dtype=torch.int64, device=dev)
-    with vp.Plan(K, M, qam, n, tau, fp64_threshold, lam=lam, demap=demap, frac_bits=frac_bits) as plan:
+    with vp.Plan(K, M, qam, n, tau, fp64_threshold, lam=lam, demap=demap, frac_bits=frac_bits,
+                 tensor_product=tensor_product) as plan:
         vp.vp_factorize(plan.handle, Hd, C, U, P, ul, st)
         if uniform_S is not None:
             vp.vp_precode(plan.handle, symd, uniform_S, None, V, x, l, g)
