@@ -304,10 +304,11 @@ def profiled_traffic(kernel_file: str) -> dict | None:
 
 def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
     """Uneven batch: 20,000 problems x 14 vectors, (K x M, Q, n) uniform over
-    {4x8, 8x16, 12x16, 16x16} x {16, 64, 256} x {16, 64, 256, 1024}. Three
-    ways: the grouped launches of vp_batch_launch, the same captured in a
-    CUDA graph, and the plain path (one vp_factorize + vp_precode per
-    problem, one plan per distinct shape)."""
+    {4x8, 8x16, 12x16, 16x16} x {16, 64, 256} x {16, 64, 256, 1024}. The
+    search as one launch per K tile (the default; also captured in a CUDA
+    graph and autotuned), in one persistent launch (direct and autotuned),
+    and the plain path (one vp_factorize + vp_precode per problem, one plan
+    per distinct shape)."""
     import numpy as np
     import torch
 
@@ -340,6 +341,20 @@ def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
         return statistics.median(ts)
 
     torch.cuda.synchronize()
+    # the search in one persistent launch, heaviest first over all K tiles
+    with vp.Batch(descs, stream=stream, persistent=1) as b:
+        for _ in range(3):
+            b.launch(stream)
+        torch.cuda.synchronize()
+        ms = timed(lambda: b.launch(stream), 10)
+        out["persistent_ms"] = ms
+        out["persistent_vectors_per_s"] = V / (ms / 1e3)
+        out["persistent_launches"] = b.launches
+        out["persistent_tuned_knob"] = b.autotune(reps=3, cache="", stream=stream)[-1]
+        ms = timed(lambda: b.launch(stream), 10)
+        out["persistent_tuned_ms"] = ms
+    # the search as one launch per K tile (the default); direct, in a CUDA
+    # graph, and autotuned
     with vp.Batch(descs, stream=stream) as b:
         for _ in range(3):
             b.launch(stream)
@@ -361,7 +376,14 @@ def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
         out["graph_ms"] = ms
         out["graph_vectors_per_s"] = V / (ms / 1e3)
         del graph
-        # the project's autotuner (vp_batch_autotune): per-group mapping knobs, same outputs
+        # the project's autotuner (vp_batch_autotune): per-group mapping knobs,
+        # same outputs; against one generic mapping (two warps per channel's
+        # path lists, four warps per search block) and the built-in choices
+        stages = [gi[0] for gi in vp.vp_batch_group_info(b.handle)]
+        vp.vp_batch_set_tuning(b.handle, [64 if st == 1 else (4 if st == 2 else 0) for st in stages])
+        ms = timed(lambda: b.launch(stream), 10)
+        out["generic_mapping_ms"] = ms
+        vp.vp_batch_set_tuning(b.handle, [0] * len(stages))
         out["tuned_knobs"] = b.autotune(reps=3, cache="", stream=stream)
         for _ in range(3):
             b.launch(stream)

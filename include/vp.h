@@ -320,7 +320,7 @@ size_t vp_batch_workspace_bytes(const vp_batch* batch);
 vp_status vp_batch_bind(vp_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Run the whole batch: enqueue one memset and the grouped kernel launches
+ * Run the whole batch: enqueue memsets and the kernel launches
  * (vp_batch_launch_count of them) on `stream`; no host synchronisation, no
  * allocation and no host-to-device copy. Inputs are read and outputs written
  * through the descriptors' pointers. Returns VP_ERR_NOT_FACTORIZED if the
@@ -332,12 +332,34 @@ vp_status vp_batch_launch(vp_batch* batch, void* stream);
 int vp_batch_launch_count(const vp_batch* batch);
 
 /*
+ * How vp_batch_launch runs the search (Alg. 2's post-processing) of the
+ * batch:
+ *   0  (the default) one launch per K tile (2, 4, 8, 12, 16), heaviest
+ *      first inside each;
+ *   1  one persistent launch for all problems: resident blocks take
+ *      problems from a device counter, heaviest first (S * n_paths * K^2),
+ *      each with the search body of its K tile, so that tiles of different
+ *      size fill each other's tails.
+ * The outputs are the same. Factorisation and path selection run grouped
+ * by (K, M) and by path-count class either way.
+ */
+vp_status vp_batch_set_persistent(vp_batch* batch, int persistent);
+
+/*
  * Autotuner. Every path-selection and search launch of a batch (a "group")
- * has one mapping knob: the threads that work on one channel's path lists
- * (32, 64, 128 or 256) and the warps per block of the search (1..7, i.e. the
- * data vectors of a problem in flight at once); 0 is the built-in choice.
- * The knobs change how the work maps to lanes, never the arithmetic: the
- * outputs are the same for every setting.
+ * has one mapping knob (0 is the built-in choice):
+ *   path selection: the threads that work on one channel's path lists
+ *     (32, 64, 128 or 256);
+ *   search of one K tile: warps per block (1..7, the data vectors of a
+ *     problem in flight at once);
+ *   persistent search (stage 3): warps per block (bits 0-2, 0 or 1..7)
+ *     | resident blocks per SM (bits 3-5: 0 = as many as fit, 1..4: the
+ *     problems in flight per SM) | staging of the 16-level tile's path codes
+ *     (bits 6-7: 0 by the shared-memory budget, 1 staged in shared memory,
+ *     2 read in place from global memory).
+ * The knobs change how the work maps to lanes, blocks and memory, never the
+ * arithmetic: the outputs are the same for every setting. Groups of the
+ * search form not in use (see vp_batch_set_persistent) are not timed.
  *
  * vp_batch_autotune runs the bound batch once, then times each group alone
  * under every candidate (reps launches each, CUDA events on `stream`) and
@@ -358,9 +380,10 @@ int vp_batch_get_tuning(const vp_batch* batch, int* knobs, int max_knobs);
 vp_status vp_batch_set_tuning(vp_batch* batch, const int* knobs, int n_knobs);
 
 /* Shape of each group, for keying a tuning cache: 6 ints per group in the
- * HOST array `info` (stage 0 factor / 1 paths / 2 search, problem count,
- * K (factor) or K tile (search) else 0, M (factor) else 0, largest n_paths,
- * largest S); returns the group count (-1 for NULL). */
+ * HOST array `info` (stage 0 factor / 1 paths / 2 search of one K tile /
+ * 3 persistent search, problem count, K (factor) or K tile (stage 2) else 0,
+ * M (factor) else 0, largest n_paths, largest S); returns the group count
+ * (-1 for NULL). */
 int vp_batch_group_info(const vp_batch* batch, int* info, int max_groups);
 
 /* Free the batch (host memory only; the workspace stays the caller's). */

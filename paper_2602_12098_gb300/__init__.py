@@ -31,7 +31,7 @@ __all__ = [
     "vp_job_desc", "vp_job_done", "vp_server_stats", "vp_server_create", "vp_server_submit", "vp_server_poll",
     "vp_server_drain", "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "Server",
     "vp_batch_autotune", "vp_batch_get_tuning", "vp_batch_set_tuning", "vp_batch_group_info",
-    "vp_server_create_fake", "EXPORTED_SYMBOLS", "Plan",
+    "vp_server_create_fake", "vp_batch_set_persistent", "EXPORTED_SYMBOLS", "Plan",
 ]
 
 VP_CH_NONFINITE = 1
@@ -56,7 +56,7 @@ EXPORTED_SYMBOLS = (
     "vp_batch_bind", "vp_batch_launch", "vp_batch_launch_count", "vp_batch_destroy", "vp_precode_batch",
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
     "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "vp_batch_autotune", "vp_batch_get_tuning",
-    "vp_batch_set_tuning", "vp_batch_group_info", "vp_server_create_fake",
+    "vp_batch_set_tuning", "vp_batch_group_info", "vp_server_create_fake", "vp_batch_set_persistent",
 )
 
 
@@ -141,6 +141,8 @@ def load():
             L.vp_batch_workspace_bytes.restype = ctypes.c_size_t
             L.vp_batch_bind.argtypes = [vpp, vpp, ctypes.c_size_t, vpp]
             L.vp_batch_launch.argtypes = [vpp, vpp]
+            L.vp_batch_set_persistent.argtypes = [vpp, ctypes.c_int]
+            L.vp_batch_set_persistent.restype = ctypes.c_int
             L.vp_batch_launch_count.argtypes = [vpp]
             L.vp_batch_launch_count.restype = ctypes.c_int
             L.vp_batch_destroy.argtypes = [vpp]
@@ -360,10 +362,12 @@ def packed_descs(pk, H, sym, x, l, gamma, status=None, tau=0.0):
 class Batch:
     """Owning handle of a vp_batch and its device workspace (a torch uint8 tensor)."""
 
-    def __init__(self, descs, fp64_threshold: float = 1e4, stream=None):
+    def __init__(self, descs, fp64_threshold: float = 1e4, stream=None, persistent: int = 0):
         import torch
         self.descs = _desc_array(descs)
         self.handle = vp_batch_create(self.descs, fp64_threshold)
+        if persistent:
+            vp_batch_set_persistent(self.handle, persistent)
         nbytes = vp_batch_workspace_bytes(self.handle)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.workspace.data_ptr()
@@ -415,6 +419,10 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def vp_batch_set_persistent(batch: int, persistent: int) -> None:
+    _check(load().vp_batch_set_persistent(batch, int(persistent)), "vp_batch_set_persistent")
 
 
 def vp_batch_autotune(batch: int, reps: int = 3, stream=None) -> None:

@@ -22,17 +22,26 @@
 
 struct vp_batch {
     struct Group {
-        int stage;   // 0 factor, 1 paths, 2 search
+        int stage;   // 0 factor, 1 paths, 2 search of one K tile, 3 the persistent search of all problems
         int start, count;
         int K, M, KT, n_max, km_max, s_max;
-        int knob = 0;   // tuned mapping: paths = threads per channel, search = warps per block (0 = default)
+        // tuned mapping (0 = built in): paths = threads per channel; search of
+        // a K tile = warps per block; persistent search = warps per block
+        // (bits 0-2) | resident blocks per SM (bits 3-5) | staging of the
+        // 16-level tile's path codes, 1 shared memory 2 in place (bits 6-7)
+        int knob = 0;
     };
     std::vector<vp_problem_desc> descs;
     std::vector<vp::BatchProblem> table;   // device pointers filled in by bind
-    std::vector<int> ids;                  // [3][n]: factor, paths, search order
+    std::vector<int> ids;                  // [4][n]: factor, paths, search order per K tile, search order
     std::vector<size_t> state_off;         // per problem, from the state base
     std::vector<Group> groups;
     float kappa_thr = 1e4f;
+    // the search stage in one persistent launch over all problems (heaviest
+    // first, all K tiles: the stage-3 group), or one launch per K tile (the
+    // default: faster on GB300 for the 20,000-problem mix, 4.82 vs 5.05 ms)
+    int persistent = 0;
+    int km_all = 0, n_all = 0, s_all = 0;
     size_t off_table = 0, off_ids = 0, off_nflag = 0, off_flags = 0, off_state = 0, bytes = 0;
     unsigned char* ws = nullptr;
 };
@@ -67,7 +76,7 @@ vp_status plan_batch(const vp_problem_desc* descs, int n, float thr, vp_batch* b
     b->descs.assign(descs, descs + n);
     b->kappa_thr = thr;
     const size_t N = (size_t)n;
-    b->ids.assign(3 * N, 0);
+    b->ids.assign(4 * N, 0);
     b->state_off.assign(N, 0);
     size_t st = 0;
     for (size_t i = 0; i < N; ++i) {
@@ -139,9 +148,23 @@ vp_status plan_batch(const vp_problem_desc* descs, int n, float thr, vp_batch* b
     }
     std::copy(o.begin(), o.end(), b->ids.begin() + 2 * N);
 
+    // the persistent search: heaviest first over all problems
+    o = idx;
+    std::stable_sort(o.begin(), o.end(), [&](int a, int c) { return cost(a) > cost(c); });
+    std::copy(o.begin(), o.end(), b->ids.begin() + 3 * N);
+    for (size_t i = 0; i < N; ++i) {
+        b->km_all = std::max(b->km_all, descs[i].K * descs[i].M);
+        b->n_all = std::max(b->n_all, descs[i].n_paths);
+        b->s_all = std::max(b->s_all, descs[i].S);
+    }
+    {
+        vp_batch::Group g = {3, 0, (int)N, 0, 0, 0, b->n_all, b->km_all, b->s_all};
+        b->groups.push_back(g);
+    }
+
     b->off_table = 0;
     b->off_ids = align_up(sizeof(vp::BatchProblem) * N, 256);
-    b->off_nflag = b->off_ids + align_up(sizeof(int) * 3 * N, 256);
+    b->off_nflag = b->off_ids + align_up(sizeof(int) * 4 * N, 256);
     b->off_flags = b->off_nflag + 256;
     b->off_state = b->off_flags + align_up(sizeof(int) * N, 256);
     b->bytes = b->off_state + st;
@@ -200,6 +223,23 @@ void fill_table(vp_batch* b)
     }
 }
 
+// One search group: a K tile's launch (stage 2), or the persistent launch of
+// every problem (stage 3, its counter reset first).
+cudaError_t launch_search_group(const vp_batch* b, const vp_batch::Group& g, cudaStream_t s)
+{
+    const int N = (int)b->descs.size();
+    const vp::BatchProblem* probs = reinterpret_cast<const vp::BatchProblem*>(b->ws + b->off_table);
+    const int* ids = reinterpret_cast<const int*>(b->ws + b->off_ids);
+    if (g.stage == 2)
+        return vp::launch_search_batch(probs, ids + 2 * N + g.start, g.count, g.KT, g.km_max, g.n_max, g.s_max, s,
+                                       g.knob);
+    int* counter = reinterpret_cast<int*>(b->ws + b->off_nflag) + 1;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    return vp::launch_search_persist(probs, ids + 3 * N, g.count, g.km_max, g.n_max, g.s_max, counter, s,
+                                     g.knob & 7, (g.knob >> 3) & 7, (g.knob >> 6) & 3);
+}
+
 }  // namespace
 
 extern "C" {
@@ -240,7 +280,7 @@ vp_status vp_batch_bind(vp_batch* b, void* workspace, size_t workspace_bytes, vo
     const size_t N = b->descs.size();
     if (cudaMemcpyAsync(b->ws + b->off_table, b->table.data(), sizeof(vp::BatchProblem) * N, cudaMemcpyHostToDevice,
                         s) != cudaSuccess ||
-        cudaMemcpyAsync(b->ws + b->off_ids, b->ids.data(), sizeof(int) * 3 * N, cudaMemcpyHostToDevice, s) !=
+        cudaMemcpyAsync(b->ws + b->off_ids, b->ids.data(), sizeof(int) * 4 * N, cudaMemcpyHostToDevice, s) !=
             cudaSuccess) {
         b->ws = nullptr;
         return VP_ERR_CUDA;
@@ -269,9 +309,14 @@ vp_status vp_batch_launch(vp_batch* b, void* stream)
                                 cudaSuccess)
             return VP_ERR_CUDA;
     for (const vp_batch::Group& g : b->groups)
-        if (g.stage == 2 && vp::launch_search_batch(probs, ids + 2 * N + g.start, g.count, g.KT, g.km_max, g.n_max,
-                                                    g.s_max, s, g.knob) != cudaSuccess)
-            return VP_ERR_CUDA;
+        if (g.stage == (b->persistent ? 3 : 2) && launch_search_group(b, g, s) != cudaSuccess) return VP_ERR_CUDA;
+    return VP_OK;
+}
+
+vp_status vp_batch_set_persistent(vp_batch* b, int persistent)
+{
+    if (!b || (persistent != 0 && persistent != 1)) return VP_ERR_INVALID_ARG;
+    b->persistent = persistent;
     return VP_OK;
 }
 
@@ -281,6 +326,7 @@ static bool knob_ok(int stage, int v)
     if (v == 0) return true;
     if (stage == 1) return v == 32 || v == 64 || v == 128 || v == 256;
     if (stage == 2) return v >= 1 && v <= 7;
+    if (stage == 3) return v > 0 && v < 256 && ((v >> 3) & 7) <= 4 && ((v >> 6) & 3) <= 2;
     return false;
 }
 
@@ -304,20 +350,31 @@ vp_status vp_batch_autotune(vp_batch* b, int reps, void* stream)
     }
     static const int kPaths[] = {32, 64, 128, 256};
     static const int kWarps[] = {4, 5, 6, 7};
+    // persistent search: warps per block x resident blocks per SM x staging
+    std::vector<int> kPersist;
+    for (int nw : {0, 6, 7})
+        for (int bps : {0, 2, 3})
+            for (int stg : {0, 1, 2}) kPersist.push_back(nw | (bps << 3) | (stg << 6));
     st = VP_OK;
     for (vp_batch::Group& g : b->groups) {
-        if (g.stage == 0) continue;
-        const int* cand = g.stage == 1 ? kPaths : kWarps;
+        if (g.stage == 0 || g.stage == (b->persistent ? 2 : 3)) continue;
+        std::vector<int> cand;
+        if (g.stage == 1) cand.assign(kPaths, kPaths + 4);
+        else if (g.stage == 2) cand.assign(kWarps, kWarps + 4);
+        else cand = kPersist;
         float best = INFINITY;
         int best_v = 0;
-        for (int ci = -1; ci < 4 && st == VP_OK; ++ci) {
+        for (int ci = -1; ci < (int)cand.size() && st == VP_OK; ++ci) {
             const int v = ci < 0 ? 0 : cand[ci];
             float ms = 0.f;
             cudaError_t e = cudaEventRecord(e0, s);
             for (int r = 0; r < reps && e == cudaSuccess; ++r) {
                 if (g.stage == 1) e = vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, s, v);
-                else e = vp::launch_search_batch(probs, ids + 2 * N + g.start, g.count, g.KT, g.km_max, g.n_max,
-                                                 g.s_max, s, v);
+                else {
+                    vp_batch::Group gv = g;
+                    gv.knob = v;
+                    e = launch_search_group(b, gv, s);
+                }
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -362,7 +419,7 @@ int vp_batch_group_info(const vp_batch* b, int* info, int max_groups)
         int* o = info + 6 * i;
         o[0] = g.stage;
         o[1] = g.count;
-        o[2] = g.stage == 0 ? g.K : (g.stage == 2 ? g.KT : 0);
+        o[2] = g.stage == 0 ? g.K : (g.stage == 2 ? g.KT : 0);   // stage 3: every K tile
         o[3] = g.stage == 0 ? g.M : 0;
         o[4] = g.n_max;
         o[5] = g.s_max;
@@ -370,7 +427,14 @@ int vp_batch_group_info(const vp_batch* b, int* info, int max_groups)
     return n;
 }
 
-int vp_batch_launch_count(const vp_batch* b) { return b ? (int)b->groups.size() + 1 : 0; }
+int vp_batch_launch_count(const vp_batch* b)
+{
+    if (!b) return 0;
+    int n = 1;   // the FP64 fix-up
+    for (const vp_batch::Group& g : b->groups)
+        if (g.stage < 2 || g.stage == (b->persistent ? 3 : 2)) ++n;
+    return n;
+}
 
 vp_status vp_batch_destroy(vp_batch* b)
 {

@@ -222,6 +222,15 @@ cudaError_t launch_pathsel_batch(const BatchProblem* probs, const int* ids, int 
 // nw: warps per block (1..7; 0 = chosen from s_max)
 cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int count, int KT, int km_max,
                                 int n_max, int s_max, cudaStream_t s, int nw = 0);
+// The whole search stage of a batch in one persistent launch: ids[0..count)
+// in the order taken (heaviest first), problems of every K tile; `counter` is
+// a device int that must be 0 at launch. Knobs (0 = built in): nw warps per
+// block (1..7), blocks_per_sm resident (1..4: problems in flight per SM),
+// stage16 = 1 stage the 16-level tile's path codes in shared memory, 2 read
+// them in place.
+cudaError_t launch_search_persist(const BatchProblem* probs, const int* ids, int count, int km_max, int n_max,
+                                  int s_max, int* counter, cudaStream_t s, int nw = 0, int blocks_per_sm = 0,
+                                  int stage16 = 0);
 
 // ---------------------------------------------------------------------------
 // Small device helpers shared by the kernels of this library.

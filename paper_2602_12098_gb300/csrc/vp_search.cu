@@ -336,11 +336,9 @@ __host__ __device__ inline SearchSmem search_smem(int KT, int KM, int NP, int NW
 // arithmetic per path is the same as a full descent, so results are
 // identical; the shared levels are the ones with the most column updates.
 template <int KT, bool BATCH, bool LUT, bool FIX, bool GP, bool TC>
-__global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
+__device__ __forceinline__ void search_block(const SearchArgs& a, int c, unsigned char* smraw)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
     const int NW = blockDim.x >> 5;
-    const int c = blockIdx.x;
     int K, M, Mp, n, nch, m_qam;
     float tau, inv_tau;
     int v0, v1;
@@ -593,6 +591,47 @@ __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
                 __syncwarp(kFull);
             }
             if (pair_rows) pair_rows_out(pt, ptl, ulv, upk, K, M, Mp, v, v + NW, v1, xo, go);
+        }
+    }
+}
+
+template <int KT, bool BATCH, bool LUT, bool FIX, bool GP, bool TC>
+__global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    search_block<KT, BATCH, LUT, FIX, GP, TC>(a, blockIdx.x, smraw);
+}
+
+// One problem of a persistent launch, as its own function (each K tile keeps
+// the register allocation of its plain kernel; the call is once per problem).
+template <int KT, bool GP>
+__device__ __noinline__ void search_item(const SearchArgs& a, int c, unsigned char* smraw)
+{
+    search_block<KT, true, false, false, GP, false>(a, c, smraw);
+}
+
+// Uneven batches in one persistent launch: resident blocks take problems
+// from a device counter in the order of a.ids (heaviest first, all K tiles
+// mixed), each with the search body of its K tile; the shared-memory layout
+// of every tile fits the launch's (sized for the largest). GP16: the 16-level
+// tile reads the path codes in place.
+template <bool GP16>
+__global__ void __launch_bounds__(224, 4) search_persist_kernel(SearchArgs a, int* counter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int c = item;
+        __syncthreads();                     // every thread has read the item (and left the last one's smem)
+        if (c >= a.C) break;
+        switch (search_tile(a.probs[a.ids[c]].K)) {
+        case 2: search_item<2, false>(a, c, smraw); break;
+        case 4: search_item<4, false>(a, c, smraw); break;
+        case 8: search_item<8, false>(a, c, smraw); break;
+        case 12: search_item<12, false>(a, c, smraw); break;
+        default: search_item<16, GP16>(a, c, smraw); break;
         }
     }
 }
@@ -899,6 +938,43 @@ cudaError_t launch_search(const vp_plan* p, const uint8_t* sym, int S, const int
     if (K <= 8) return launch_kt<8>(a, p->C, threads, s);
     if (K <= 12) return launch_kt<12>(a, p->C, threads, s);
     return launch_kt<16>(a, p->C, threads, s);
+}
+
+cudaError_t launch_search_persist(const BatchProblem* probs, const int* ids, int count, int km_max, int n_max,
+                                  int s_max, int* counter, cudaStream_t s, int nw_set, int blocks_per_sm, int stage16)
+{
+    SearchArgs a = SearchArgs();
+    a.probs = probs;
+    a.ids = ids;
+    a.C = count;
+    a.KM = km_max;
+    a.NP = n_max;
+    int nw = 7;
+    if (s_max <= 7) nw = s_max < 1 ? 1 : s_max;
+    else if (s_max % 7 != 0 && s_max % 6 == 0) nw = 6;
+    if (nw_set >= 1 && nw_set <= 7) nw = nw_set;
+    // the 16-level tile stages its path codes (stage16 = 1), reads them in
+    // place (2), or decides by the budget of four blocks per SM (0)
+    bool gp16 = search_smem(16, km_max, n_max, nw, false).total > kSearchSmemBudget;
+    if (stage16 == 1) gp16 = false;
+    if (stage16 == 2) gp16 = true;
+    int sh = search_smem(16, km_max, n_max, nw, gp16).total;
+    for (int kt : {2, 4, 8, 12}) sh = max(sh, search_smem(kt, km_max, n_max, nw, false).total);
+    const void* fn = gp16 ? reinterpret_cast<const void*>(search_persist_kernel<true>)
+                          : reinterpret_cast<const void*>(search_persist_kernel<false>);
+    cudaError_t e = allow_dynamic_smem(fn, (size_t)sh);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nw * 32, (size_t)sh)) != cudaSuccess) return e;
+    if (blocks_per_sm >= 1 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    int grid = sms * (per_sm < 1 ? 1 : per_sm);
+    if (grid > count) grid = count;
+    if (grid < 1) return cudaSuccess;
+    if (gp16) search_persist_kernel<true><<<grid, nw * 32, sh, s>>>(a, counter);
+    else search_persist_kernel<false><<<grid, nw * 32, sh, s>>>(a, counter);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_search_batch(const BatchProblem* probs, const int* ids, int count, int KT, int km_max,

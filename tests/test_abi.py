@@ -86,8 +86,23 @@ def test_batch_validation_and_grouping():
     b = vp.vp_batch_create(good)
     try:
         # factor: (4,8), (8,16), (12,16), (16,16); paths: n classes 16, 64, 256, 1024;
-        # search: K tiles 4, 8, 12, 16; plus the FP64 fix-up
+        # search: K tiles 4, 8, 12, 16 (the default) or one persistent launch;
+        # plus the FP64 fix-up
         assert vp.vp_batch_launch_count(b) == 4 + 4 + 4 + 1
+        vp.vp_batch_set_persistent(b, 1)
+        assert vp.vp_batch_launch_count(b) == 4 + 4 + 1 + 1
+        vp.vp_batch_set_persistent(b, 0)
+        with pytest.raises(vp.VPError):
+            vp.vp_batch_set_persistent(b, 2)
+        info = vp.vp_batch_group_info(b)
+        assert [g[0] for g in info] == [0] * 4 + [1] * 4 + [2] * 4 + [3]
+        assert info[-1][1] == len(good) and info[-1][4] == 1024 and info[-1][5] == 14
+        knobs = vp.vp_batch_get_tuning(b)
+        assert len(knobs) == 13
+        for bad in (5 << 3, 3 << 6, 256, -1):             # no such blocks / staging value
+            with pytest.raises(vp.VPError):
+                vp.vp_batch_set_tuning(b, knobs[:-1] + [bad])
+        vp.vp_batch_set_tuning(b, knobs[:-1] + [7 | (2 << 3) | (1 << 6)])
         ws = vp.vp_batch_workspace_bytes(b)
         assert ws == vp.vp_precode_batch_workspace_bytes(good)
         with pytest.raises(vp.VPError) as e:          # never bound to a workspace
@@ -183,15 +198,18 @@ def test_batch_tuning_knobs_host_side():
     try:
         info = vp.vp_batch_group_info(b)
         stages = [g[0] for g in info]
-        assert stages == sorted(stages) and set(stages) == {0, 1, 2}
-        assert len(info) == vp.vp_batch_launch_count(b) - 1
+        assert stages == sorted(stages) and set(stages) == {0, 1, 2, 3}
+        # every group is one launch except the form of the search not in use
+        assert len(info) == vp.vp_batch_launch_count(b) - 1 + stages.count(3)
         assert vp.vp_batch_get_tuning(b) == [0] * len(info)
-        knobs = [0 if st == 0 else (128 if st == 1 else 5) for st in stages]
+        knob = {0: 0, 1: 128, 2: 5, 3: 6 | (2 << 3) | (2 << 6)}
+        knobs = [knob[st] for st in stages]
         vp.vp_batch_set_tuning(b, knobs)
         assert vp.vp_batch_get_tuning(b) == knobs
-        for bad in (knobs[:-1], [0 if st == 0 else (48 if st == 1 else 5) for st in stages],
-                    [0 if st == 0 else (64 if st == 1 else 8) for st in stages],
-                    [7 if st == 0 else 0 for st in stages]):
+        for bad in (knobs[:-1], [48 if st == 1 else knob[st] for st in stages],
+                    [8 if st == 2 else knob[st] for st in stages],
+                    [7 if st == 0 else knob[st] for st in stages],
+                    [(3 << 6) if st == 3 else knob[st] for st in stages]):
             with pytest.raises(vp.VPError) as e:
                 vp.vp_batch_set_tuning(b, bad)
             assert e.value.code == 1

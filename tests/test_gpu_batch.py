@@ -202,7 +202,7 @@ def test_autotuned_launch_equals_default_and_cache_roundtrip(tmp_path):
     cache = str(tmp_path / "tune.json")
     with vp.Batch(t.descs) as b:
         knobs = b.autotune(reps=2, cache=cache)
-        assert len(knobs) == vp.vp_batch_launch_count(b.handle) - 1
+        assert len(knobs) == len(vp.vp_batch_group_info(b.handle))
         b.launch()
         t.fetch()
     assert np.array_equal(a.x_np, t.x_np) and np.array_equal(a.l_np, t.l_np)
@@ -220,3 +220,26 @@ def test_autotuned_launch_equals_default_and_cache_roundtrip(tmp_path):
         b.launch()
         c.fetch()
     assert np.array_equal(a.x_np, c.x_np) and np.array_equal(a.l_np, c.l_np) and np.array_equal(a.g_np, c.g_np)
+
+
+def test_persistent_search_equals_grouped_launches():
+    """The search in one persistent launch (heaviest first over all K tiles)
+    gives the same outputs, bit for bit, as one launch per K tile (the
+    default), under every mapping of the persistent launch: warps per block,
+    resident blocks per SM, and the 16-level tile's path codes staged in
+    shared memory or read in place."""
+    probs = mixed_problems(120, 9)
+    ref = Packed(probs)
+    with vp.Batch(ref.descs) as b:
+        assert vp.vp_batch_launch_count(b.handle) > 10
+        b.launch()
+        ref.fetch()
+    for knob in (0, 7 | (1 << 3), 6 | (2 << 3) | (1 << 6), 5 | (3 << 3) | (2 << 6)):
+        got = Packed(probs)
+        with vp.Batch(got.descs, persistent=1) as b:
+            stages = [g[0] for g in vp.vp_batch_group_info(b.handle)]
+            vp.vp_batch_set_tuning(b.handle, [knob if st == 3 else 0 for st in stages])
+            b.launch()
+            got.fetch()
+        assert np.array_equal(ref.x_np, got.x_np) and np.array_equal(ref.l_np, got.l_np)
+        assert np.array_equal(ref.g_np, got.g_np) and np.array_equal(ref.st_np, got.st_np)
