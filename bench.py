@@ -47,10 +47,10 @@ def parse():
                     help="run a reduced slot (profiling captures); the default is the full slot")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
-    ap.add_argument("--serving-slots", type=int, default=10000)
-    ap.add_argument("--serving-paths", type=int, default=64)
+    ap.add_argument("--serving-slots", type=int, default=2000)
+    ap.add_argument("--serving-paths", type=int, nargs="+", default=[64, 256])
     ap.add_argument("--serving-lanes", type=int, default=8)
-    ap.add_argument("--serving-pool-mib", type=int, default=256)
+    ap.add_argument("--serving-pool-mib", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -607,81 +607,126 @@ def measure_paper_points(dev, flush, steps: int) -> list:
     return res
 
 
-def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 256, n_paths: int = 64) -> dict:
-    """Open-loop serving through the job server (vp_server_*): Poisson job
-    arrivals (mean 4 per 0.5 ms slot); a job is one cell's slot, 3276
-    subcarriers x 14 symbols, K in {4, 8, 12, 16}, M = 16, Q in {16, 64, 256},
-    n = 64, iid channels. Each job is submitted at its arrival time; the
-    server admits it when one of `lanes` streams is idle and its state fits
-    in the `pool_mib` pool, oldest first. Latency = the job's device end time
-    - its arrival, both from the server's clock zero. Inputs are one draw per
-    job type, reused by its jobs (timing only: outputs rotate over `lanes`
-    buffers per type)."""
-    import numpy as np
+def serving_inputs(dev, jobs, ring: int) -> dict:
+    """Device inputs of a Poisson job trace: per job type (K, M, qam), `ring`
+    independent draws (those of the type's first `ring` jobs) with their own
+    output buffers; the k-th job of a type reads draw k mod ring and writes
+    output set k mod ring. The caller keeps the returned tensors alive while
+    any descriptor that points at them is in use."""
+    import torch
+
+    from paper_2602_12098_gb300 import workloads as W
+    sets = {}
+    for j in jobs:
+        t = (j.K, j.M, j.qam)
+        sets.setdefault(t, [])
+        if len(sets[t]) < ring:
+            Hn, sn = W.job_inputs(j)
+            V = sn.shape[0]
+            sets[t].append((torch.from_numpy(Hn).to(dev), torch.from_numpy(sn).to(dev),
+                            torch.empty((V, j.M), dtype=torch.complex64, device=dev),
+                            torch.empty((V, j.K, 2), dtype=torch.int8, device=dev),
+                            torch.empty((V,), dtype=torch.float32, device=dev)))
+    torch.cuda.synchronize()
+    return sets
+
+
+def serving_outputs_match(dev, sets, last_of: dict, n: int) -> int:
+    """Checks the outputs a trace left behind: for every (type, ring slot)
+    the last job that wrote it must equal the plan path (vp_factorize +
+    vp_precode) on the same inputs, bit for bit. Returns the number checked;
+    raises on a mismatch."""
     import torch
 
     import paper_2602_12098_gb300 as vp
+    checked = 0
+    for (t, k), _ in sorted(last_of.items()):
+        K, M, qam = t
+        H, sym, x, l, g = sets[t][k]
+        C, V = H.shape[0], sym.shape[0]
+        x2, l2, g2 = torch.empty_like(x), torch.empty_like(l), torch.empty_like(g)
+        with vp.Plan(K, M, qam, n) as plan:
+            vp.vp_factorize(plan.handle, H, C)
+            vp.vp_precode(plan.handle, sym, V // C, None, V, x2, l2, g2)
+            torch.cuda.synchronize()
+        if not (torch.equal(l, l2) and torch.equal(x, x2) and torch.equal(g, g2)):
+            raise RuntimeError(f"serving: outputs of a {t} job differ from the plan path")
+        checked += 1
+    return checked
+
+
+def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 1024, n_paths=(64, 256),
+                    loads=(0.5, 1.0, 2.0, 4.0), ring: int = 8) -> dict:
+    """Open-loop serving through the job server (vp_server_*): Poisson job
+    arrivals at `loads` mean jobs per 0.5 ms slot; a job is one cell's slot,
+    3276 subcarriers x 14 symbols, K in {4, 8, 12, 16}, M = 16, Q in {16, 64,
+    256}, iid channels, at each path count in `n_paths`, under both admission
+    policies. Each trace is replayed by vp_server_replay (a C++ loop submits
+    each job when the host clock reaches its arrival time), so host dispatch
+    lag (submission - arrival) is reported apart from device latency (end -
+    submission); job latency = end - arrival, on the server's clock. Inputs:
+    `ring` independent draws per job type (see serving_inputs); after each
+    trace the outputs left in every ring slot are checked against the plan
+    path. `capacity_vectors_per_s` is the same jobs submitted all at once."""
+    import numpy as np
+
+    import paper_2602_12098_gb300 as vp
     from paper_2602_12098_gb300 import workloads as W
-    jobs = W.poisson_jobs(n_slots, n_paths=n_paths)
-    types = sorted({(j.K, j.M, j.qam, j.n_paths) for j in jobs})
-    bufs = {}
-    for t in types:
-        K, M, qam, n = t
-        proto = next(j for j in jobs if (j.K, j.M, j.qam, j.n_paths) == t)
-        Hn, sn = W.job_inputs(proto)
-        C, V = Hn.shape[0], sn.shape[0]
-        H, sym = torch.from_numpy(Hn).to(dev), torch.from_numpy(sn).to(dev)
-        outs = [(torch.empty((V, M), dtype=torch.complex64, device=dev),
-                 torch.empty((V, K, 2), dtype=torch.int8, device=dev),
-                 torch.empty((V,), dtype=torch.float32, device=dev)) for _ in range(lanes)]
-        bufs[t] = {"V": V, "descs": [vp.job_desc(K, M, qam, n, C, proto.symbols, H, sym, x, l, g)
-                                     for x, l, g in outs], "used": 0}
-    torch.cuda.synchronize()
-    with vp.Server(pool_mib << 20, lanes) as srv:
-        for t in types:                      # warm-up: every job type once
-            for d in bufs[t]["descs"]:
-                srv.submit(d)
-        srv.drain(60.0)
-        srv.poll()
-        arrive = {}
-        done = {}
-        srv.reset_clock()
-        t0 = time.perf_counter()
-        late = 0.0
-        for j in jobs:
-            target = t0 + j.arrival_us * 1e-6
-            while True:
-                now = time.perf_counter()
-                if now >= target:
-                    break
-                for rec in srv.poll():
-                    done[rec[0]] = rec
-            late = max(late, now - target)
-            bb = bufs[(j.K, j.M, j.qam, j.n_paths)]
-            jid = srv.submit(bb["descs"][bb["used"] % lanes])
-            bb["used"] += 1
-            arrive[jid] = (j.arrival_us * 1e-3, bb["V"])
-        srv.drain(600.0)
-        for rec in srv.poll():
-            done[rec[0]] = rec
-        st = srv.stats()
-    if sorted(done) != sorted(arrive) or any(rec[1] != 0 for rec in done.values()):
-        raise RuntimeError("serving: a job failed or was not reported")
-    lat = np.array([done[i][3] - arrive[i][0] for i in arrive])
-    wait = np.array([done[i][2] - arrive[i][0] for i in arrive])
-    end = max(rec[3] for rec in done.values())
-    vecs = sum(v for _, v in arrive.values())
-    return {"workload": f"Poisson arrivals, mean 4 jobs per 0.5 ms slot, {n_slots} slots; job = 3276 subcarriers "
-                        f"x 14 symbols, K in {{4,8,12,16}}, M 16, Q in {{16,64,256}}, n {n_paths}, iid",
-            "engine": f"vp_server: {lanes} lanes (streams), {pool_mib} MiB state pool, first come first served "
-                      "admission by idle lane and pool space",
-            "jobs": len(jobs), "p50_job_ms": float(np.percentile(lat, 50)), "p99_job_ms": float(np.percentile(lat, 99)),
-            "p50_admission_wait_ms": float(np.percentile(wait, 50)),
-            "deadline_ms": 0.5, "deadline_miss_frac": float(np.mean(lat > 0.5)),
-            "vectors_per_s": vecs / (end / 1e3),
-            "offered_vectors_per_s": vecs / (jobs[-1].arrival_us * 1e-6),
-            "max_in_flight": st["max_in_flight"], "pool_high_water_mib": st["pool_high_water"] / 2**20,
-            "max_dispatch_lag_ms": 1e3 * late}
+    out = {"workload": f"Poisson arrivals over {n_slots} slots of 0.5 ms; job = 3276 subcarriers x 14 symbols, "
+                       "K in {4,8,12,16}, M 16, Q in {16,64,256}, iid",
+           "engine": f"vp_server: {lanes} lanes (streams), {pool_mib} MiB state pool, first come first served "
+                     "admission by idle lane and pool space; traces replayed by vp_server_replay",
+           "deadline_ms": 0.5, "runs": []}
+    names = {vp.VP_SERVE_FCFS: "fcfs", vp.VP_SERVE_AGE_PRIORITY: "age_priority"}
+    pct = lambda a, q: float(np.percentile(a, q))
+    for load in loads:
+        jobs = W.poisson_jobs(n_slots, mean_per_slot=load)
+        sets = serving_inputs(dev, jobs, ring)
+        slot_of, last_of, seen = [], {}, {}
+        for i, j in enumerate(jobs):
+            t = (j.K, j.M, j.qam)
+            slot_of.append(seen.get(t, 0) % ring)
+            seen[t] = seen.get(t, 0) + 1
+            last_of[(t, slot_of[-1])] = i
+        arrival = [j.arrival_us * 1e-3 for j in jobs]
+        V = sum(j.subcarriers * j.symbols for j in jobs)
+        for n in n_paths:
+            descs = []
+            for j, k in zip(jobs, slot_of):
+                H, sym, x, l, g = sets[(j.K, j.M, j.qam)][k]
+                descs.append(vp.job_desc(j.K, j.M, j.qam, n, j.subcarriers, j.symbols, H, sym, x, l, g))
+            warm = list({(j.K, j.qam): d for j, d in zip(jobs, descs)}.values())
+            cap = None
+            for policy in (vp.VP_SERVE_FCFS, vp.VP_SERVE_AGE_PRIORITY):
+                with vp.Server(pool_mib << 20, lanes) as srv:
+                    srv.set_policy(policy)
+                    srv.replay(warm, [0.0] * len(warm))                 # warm-up: every job type once
+                    if cap is None:
+                        recs, _ = srv.replay(descs, [0.0] * len(descs), timeout_s=600.0)
+                        cap = V / (max(r[3] for r in recs) / 1e3)
+                    recs, sub = srv.replay(descs, arrival, timeout_s=600.0)
+                    st = srv.stats()
+                if any(r[1] != 0 for r in recs):
+                    raise RuntimeError("serving: a job failed")
+                checked = serving_outputs_match(dev, sets, last_of, n)
+                end = np.array([r[3] for r in recs])
+                arr, subm = np.array(arrival), np.array(sub)
+                lat, dev_lat, lag = end - arr, end - subm, subm - arr
+                out["runs"].append({
+                    "n_paths": n, "jobs_per_slot": load, "jobs": len(jobs), "policy": names[policy],
+                    "p50_job_ms": pct(lat, 50), "p99_job_ms": pct(lat, 99), "max_job_ms": float(lat.max()),
+                    "deadline_miss_frac": float(np.mean(lat > 0.5)),
+                    "p50_device_ms": pct(dev_lat, 50), "p99_device_ms": pct(dev_lat, 99),
+                    "p50_dispatch_lag_ms": pct(lag, 50), "p99_dispatch_lag_ms": pct(lag, 99),
+                    "max_dispatch_lag_ms": float(lag.max()),
+                    "vectors_per_s": V / (end.max() / 1e3), "offered_vectors_per_s": V / (arr[-1] / 1e3),
+                    "capacity_vectors_per_s": cap, "outputs_checked": checked,
+                    "max_in_flight": st["max_in_flight"], "pool_high_water_mib": st["pool_high_water"] / 2**20})
+        out["inputs"] = (f"{ring} independent draws per job type with their own outputs "
+                         f"({sum(t[0].numel() * 8 + t[1].numel() for v in sets.values() for t in v) / 2**20:.0f} MiB "
+                         "of H and symbols at the last load)")
+        del sets
+    return out
 
 
 def run_gpu(args):

@@ -458,7 +458,16 @@ typedef struct {
     int status;        /* VP_OK, or VP_ERR_CUDA if a launch failed */
     float admit_ms;    /* device time of admission (its first kernel enqueued after) */
     float end_ms;      /* device time when its last kernel finished */
+    int rank;          /* priority rank of its stream under VP_SERVE_AGE_PRIORITY
+                          (0 = highest), else 0 */
 } vp_job_done;
+
+/* Admission policies (vp_server_set_policy). */
+typedef enum {
+    VP_SERVE_FCFS = 0,          /* every lane at the default stream priority */
+    VP_SERVE_AGE_PRIORITY = 1   /* a job's kernels outrank those of the jobs
+                                   admitted after it while it runs */
+} vp_serve_policy;
 
 typedef struct {
     int lanes, queued, in_flight, max_in_flight;
@@ -512,6 +521,47 @@ vp_status vp_server_drain(vp_server* srv, double timeout_s);
 
 /* Set the zero of the job times (see Time above). */
 vp_status vp_server_reset_clock(vp_server* srv);
+
+/*
+ * Choose how admitted jobs share the GPU; only while no job is waiting or
+ * running (else VP_ERR_INVALID_ARG). Admission order stays first come, first
+ * served under both policies.
+ *   VP_SERVE_FCFS          (default) all lanes at one stream priority: the
+ *                          running jobs' blocks share the SMs as the block
+ *                          scheduler picks them.
+ *   VP_SERVE_AGE_PRIORITY  each lane gets one stream per CUDA stream-priority
+ *                          level (cudaDeviceGetStreamPriorityRange); a job
+ *                          admitted while others run takes the level below the
+ *                          youngest running job's, one admitted to an idle
+ *                          server the highest, so that older jobs' pending
+ *                          blocks are scheduled first (earliest deadline first
+ *                          when every job has the same relative deadline).
+ *                          Once the levels run out, later jobs share the
+ *                          lowest. A fake server models 6 levels.
+ * VP_ERR_CUDA if the streams cannot be created (the policy stays FCFS).
+ */
+vp_status vp_server_set_policy(vp_server* srv, int policy);
+
+/*
+ * Open-loop replay of a job trace, for measuring the server under a given
+ * arrival process without the caller's own dispatch delay. The server must be
+ * idle (no job waiting or running; else VP_ERR_INVALID_ARG). Resets the clock
+ * (vp_server_reset_clock), then submits job i (HOST array `jobs`) as soon as
+ * the host clock reaches arrival_ms[i] (HOST, milliseconds from the clock
+ * zero, finite, non-decreasing), retiring and admitting jobs while it waits,
+ * and returns when every job has finished or `timeout_s` seconds after the
+ * last submission (VP_ERR_TIMEOUT; the jobs keep running and are reported by
+ * vp_server_poll). Writes job i's record to done[i] (HOST, n records) and, if
+ * `submit_ms` is not NULL, the host-clock time of its submission to
+ * submit_ms[i]; submit_ms[i] - arrival_ms[i] is the replay's own dispatch lag.
+ * The host clock reads at most the clock-zero wait's latency behind the device
+ * clock, so end_ms - arrival_ms over-states a job's latency by at most that.
+ * Every descriptor is checked before anything is submitted (the errors of
+ * vp_server_submit). The records of this replay's jobs are not reported by
+ * vp_server_poll.
+ */
+vp_status vp_server_replay(vp_server* srv, const vp_job_desc* jobs, const double* arrival_ms, int n,
+                           double timeout_s, vp_job_done* done, double* submit_ms);
 
 /* Counters of the server (HOST struct). */
 vp_status vp_server_get_stats(vp_server* srv, vp_server_stats* out);

@@ -32,6 +32,7 @@ __all__ = [
     "vp_server_drain", "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "Server",
     "vp_batch_autotune", "vp_batch_get_tuning", "vp_batch_set_tuning", "vp_batch_group_info",
     "vp_server_create_fake", "vp_batch_set_persistent", "EXPORTED_SYMBOLS", "Plan",
+    "vp_server_set_policy", "vp_server_replay", "VP_SERVE_FCFS", "VP_SERVE_AGE_PRIORITY",
 ]
 
 VP_CH_NONFINITE = 1
@@ -43,6 +44,9 @@ VP_MAX_PATHS = 1024
 
 VP_DEMAP_EXACT = 0
 VP_DEMAP_LUT = 1
+
+VP_SERVE_FCFS = 0
+VP_SERVE_AGE_PRIORITY = 1
 
 EXPORTED_SYMBOLS = (
     "vp_plan_create", "vp_plan_set_fp64_threshold", "vp_plan_set_lambda", "vp_plan_set_demap",
@@ -57,6 +61,7 @@ EXPORTED_SYMBOLS = (
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
     "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "vp_batch_autotune", "vp_batch_get_tuning",
     "vp_batch_set_tuning", "vp_batch_group_info", "vp_server_create_fake", "vp_batch_set_persistent",
+    "vp_server_set_policy", "vp_server_replay",
 )
 
 
@@ -79,7 +84,7 @@ class vp_job_desc(ctypes.Structure):
 
 class vp_job_done(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("admit_ms", ctypes.c_float),
-                ("end_ms", ctypes.c_float)]
+                ("end_ms", ctypes.c_float), ("rank", ctypes.c_int)]
 
 
 class vp_server_stats(ctypes.Structure):
@@ -159,8 +164,13 @@ def load():
             L.vp_server_reset_clock.argtypes = [sp]
             L.vp_server_get_stats.argtypes = [sp, ctypes.POINTER(vp_server_stats)]
             L.vp_server_destroy.argtypes = [sp]
+            L.vp_server_set_policy.argtypes = [sp, ctypes.c_int]
+            L.vp_server_replay.argtypes = [sp, ctypes.POINTER(vp_job_desc), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp_job_done),
+                                           ctypes.POINTER(ctypes.c_double)]
             for name in ("vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
-                         "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy"):
+                         "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy",
+                         "vp_server_set_policy", "vp_server_replay"):
                 getattr(L, name).restype = ctypes.c_int
             L.vp_batch_autotune.argtypes = [vpp, ctypes.c_int, vpp]
             L.vp_batch_autotune.restype = ctypes.c_int
@@ -480,15 +490,35 @@ def vp_server_submit(server: int, job: vp_job_desc) -> int:
 
 
 def vp_server_poll(server: int, max_done: int = 256) -> list:
-    """Finished jobs since the last poll: list of (id, status, admit_ms, end_ms)."""
+    """Finished jobs since the last poll: list of (id, status, admit_ms, end_ms, rank)."""
     buf = (vp_job_done * max(int(max_done), 1))()
     n = ctypes.c_int()
     out = []
     while True:
         _check(load().vp_server_poll(server, buf, len(buf), ctypes.byref(n)), "vp_server_poll")
-        out += [(buf[i].id, buf[i].status, buf[i].admit_ms, buf[i].end_ms) for i in range(n.value)]
+        out += [(buf[i].id, buf[i].status, buf[i].admit_ms, buf[i].end_ms, buf[i].rank) for i in range(n.value)]
         if n.value < len(buf):
             return out
+
+
+def vp_server_set_policy(server: int, policy: int) -> None:
+    _check(load().vp_server_set_policy(server, int(policy)), "vp_server_set_policy")
+
+
+def vp_server_replay(server: int, jobs: list, arrival_ms, timeout_s: float = 60.0):
+    """Replay `jobs` (vp_job_desc list) at `arrival_ms` (host-clock ms from the
+    clock zero). Returns (records, submit_ms): records[i] = (id, status,
+    admit_ms, end_ms, rank) of job i, submit_ms[i] its submission time."""
+    n = len(jobs)
+    if len(arrival_ms) != n:
+        raise ValueError("one arrival time per job")
+    descs = (vp_job_desc * max(n, 1))(*jobs)
+    arr = (ctypes.c_double * max(n, 1))(*[float(a) for a in arrival_ms])
+    done = (vp_job_done * max(n, 1))()
+    sub = (ctypes.c_double * max(n, 1))()
+    _check(load().vp_server_replay(server, descs, arr, n, float(timeout_s), done, sub), "vp_server_replay")
+    recs = [(done[i].id, done[i].status, done[i].admit_ms, done[i].end_ms, done[i].rank) for i in range(n)]
+    return recs, [sub[i] for i in range(n)]
 
 
 def vp_server_drain(server: int, timeout_s: float = 60.0) -> None:
@@ -535,6 +565,12 @@ class Server:
 
     def reset_clock(self) -> None:
         vp_server_reset_clock(self.handle)
+
+    def set_policy(self, policy: int) -> None:
+        vp_server_set_policy(self.handle, policy)
+
+    def replay(self, jobs: list, arrival_ms, timeout_s: float = 60.0):
+        return vp_server_replay(self.handle, jobs, arrival_ms, timeout_s)
 
     def stats(self) -> dict:
         return vp_server_get_stats(self.handle)

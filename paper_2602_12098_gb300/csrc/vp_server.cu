@@ -8,6 +8,7 @@
 // reporting logic on a host clock instead of the GPU (a job "runs" for its
 // channel count in microseconds), so that the scheduling can be tested, and
 // studied, without a device.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -24,6 +25,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxLanes = 32;
+constexpr int kFakeRanks = 6;   // priority ranks a fake server models under the age policy
 
 size_t round_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -77,6 +79,7 @@ struct Job {
     vp_plan plan;          // parameters; d points into the pool once admitted
     size_t bytes = 0, off = 0;
     int lane = -1;
+    int rank = 0;          // priority rank of its stream (age policy), 0 = highest
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int status = VP_OK;
     double fake_t0 = 0.0, fake_t1 = 0.0;   // host-clock run of a fake server's job (ms)
@@ -130,6 +133,9 @@ struct vp_server {
     Pool* pool = nullptr;
     std::vector<cudaStream_t> lanes;
     std::vector<int64_t> lane_job;        // job on each lane, 0 = idle
+    int policy = VP_SERVE_FCFS;
+    int nranks = 1;                       // priority ranks in use by the age policy
+    std::vector<std::vector<cudaStream_t>> ranked;   // age policy: [rank][lane], rank 0 highest priority
     std::vector<cudaEvent_t> spare_events;
     cudaEvent_t ref = nullptr;
     std::unordered_map<int64_t, Job> jobs;
@@ -165,7 +171,7 @@ void finish(vp_server* s, int64_t id, Job& j, float t0, float t1)
     if (j.bytes) s->pool->release(j.off, j.bytes);
     if (j.ev0) s->spare_events.push_back(j.ev0);
     if (j.ev1) s->spare_events.push_back(j.ev1);
-    s->finished.push_back(vp_job_done{id, j.status, t0, t1});
+    s->finished.push_back(vp_job_done{id, j.status, t0, t1, j.rank});
     s->jobs.erase(id);
     ++s->completed;
 }
@@ -203,6 +209,17 @@ void retire(vp_server* s)
     }
 }
 
+// Priority rank for a job admitted now under the age policy: one below the
+// youngest running job's (so every running job outranks it), 0 when nothing
+// runs, and the lowest rank once the ranks run out (ties then share).
+int age_rank(const vp_server* s)
+{
+    const int lowest = s->nranks - 1;
+    int r = -1;
+    for (int64_t id : s->running) r = std::max(r, s->jobs.at(id).rank);
+    return std::min(lowest, r + 1);
+}
+
 // Admit waiting jobs, oldest first, while a lane is idle and the oldest fits.
 void admit(vp_server* s)
 {
@@ -220,6 +237,7 @@ void admit(vp_server* s)
         j.lane = lane;
         s->lane_job[lane] = id;
         if (s->fake) {
+            j.rank = age_rank(s);
             j.fake_t0 = host_ms(s);
             j.fake_t1 = j.fake_t0 + 1e-3 * j.desc.C;
             s->running.push_back(id);
@@ -230,7 +248,11 @@ void admit(vp_server* s)
         j.plan.cap = j.desc.C;
         j.plan.cap_mp = vp::p_rows(&j.plan);
         j.plan.C = j.desc.C;
-        const cudaStream_t st = s->lanes[lane];
+        cudaStream_t st = s->lanes[lane];
+        if (s->policy == VP_SERVE_AGE_PRIORITY) {
+            j.rank = age_rank(s);
+            st = s->ranked[j.rank][lane];
+        }
         cudaError_t e = take_event(s, &j.ev0);
         if (e == cudaSuccess) e = take_event(s, &j.ev1);
         if (e == cudaSuccess && j.desc.ready_event)
@@ -259,6 +281,52 @@ void progress(vp_server* s)
 {
     retire(s);
     admit(s);
+}
+
+// Clock zero: an event on lane 0 that the host waits for; the host clock is
+// set when the wait returns, so host times read at most the wait's latency
+// behind device times (caller holds the lock).
+vp_status reset_ref(vp_server* s)
+{
+    if (!s->fake) {
+        if (cudaEventRecord(s->ref, s->lanes[0]) != cudaSuccess || cudaEventSynchronize(s->ref) != cudaSuccess) {
+            cudaGetLastError();
+            return VP_ERR_CUDA;
+        }
+    }
+    s->t_ref = std::chrono::steady_clock::now();
+    return VP_OK;
+}
+
+// Validation and state size of a job (no lock needed).
+vp_status prepare(const vp_server* s, const vp_job_desc& job, Job* j)
+{
+    if (!job_ok(job)) return VP_ERR_INVALID_ARG;
+    j->desc = job;
+    j->plan = plan_of(job);
+    vp::DeviceState probe;
+    j->bytes = vp::carve_state(nullptr, job.C, j->plan.K, vp::p_rows(&j->plan), j->plan.n_paths, &probe);
+    if (round_up(j->bytes) > s->pool_bytes) return VP_ERR_CAPACITY;
+    return VP_OK;
+}
+
+int64_t enqueue_job(vp_server* s, const Job& j)
+{
+    const int64_t k = s->next_id++;
+    s->jobs.emplace(k, j);
+    s->waiting.push_back(k);
+    ++s->submitted;
+    progress(s);
+    return k;
+}
+
+void destroy_streams(std::vector<cudaStream_t>& v)
+{
+    for (cudaStream_t st : v) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    v.clear();
 }
 
 }  // namespace
@@ -328,20 +396,115 @@ vp_status vp_server_create_fake(size_t pool_bytes, int lanes, vp_server** out)
 
 vp_status vp_server_submit(vp_server* s, const vp_job_desc* job, int64_t* id)
 {
-    if (!s || !job || !id || !job_ok(*job)) return VP_ERR_INVALID_ARG;
+    if (!s || !job || !id) return VP_ERR_INVALID_ARG;
     Job j;
-    j.desc = *job;
-    j.plan = plan_of(*job);
-    vp::DeviceState probe;
-    j.bytes = vp::carve_state(nullptr, job->C, j.plan.K, vp::p_rows(&j.plan), j.plan.n_paths, &probe);
-    if (round_up(j.bytes) > s->pool_bytes) return VP_ERR_CAPACITY;
+    const vp_status st = prepare(s, *job, &j);
+    if (st != VP_OK) return st;
     std::lock_guard<std::mutex> lock(s->mu);
-    const int64_t k = s->next_id++;
-    s->jobs.emplace(k, j);
-    s->waiting.push_back(k);
-    ++s->submitted;
-    *id = k;
-    progress(s);
+    *id = enqueue_job(s, j);
+    return VP_OK;
+}
+
+vp_status vp_server_set_policy(vp_server* s, int policy)
+{
+    if (!s || (policy != VP_SERVE_FCFS && policy != VP_SERVE_AGE_PRIORITY)) return VP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->running.empty() || !s->waiting.empty()) return VP_ERR_INVALID_ARG;
+    if (policy == s->policy) return VP_OK;
+    if (s->fake) {
+        s->nranks = policy == VP_SERVE_AGE_PRIORITY ? kFakeRanks : 1;
+        s->policy = policy;
+        return VP_OK;
+    }
+    for (auto& v : s->ranked) destroy_streams(v);
+    s->ranked.clear();
+    s->nranks = 1;
+    s->policy = VP_SERVE_FCFS;
+    if (policy == VP_SERVE_FCFS) return VP_OK;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return VP_ERR_CUDA;
+    }
+    // CUDA priorities: lower numbers run first; rank 0 takes `greatest`
+    const int nr = std::max(1, least - greatest + 1);
+    s->ranked.resize((size_t)nr);
+    bool ok = true;
+    for (int r = 0; ok && r < nr; ++r)
+        for (int k = 0; ok && k < s->nlanes; ++k) {
+            cudaStream_t st = nullptr;
+            ok = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest + r) == cudaSuccess;
+            if (ok) s->ranked[(size_t)r].push_back(st);
+        }
+    if (!ok) {
+        cudaGetLastError();
+        for (auto& v : s->ranked) destroy_streams(v);
+        s->ranked.clear();
+        return VP_ERR_CUDA;
+    }
+    s->nranks = nr;
+    s->policy = policy;
+    return VP_OK;
+}
+
+vp_status vp_server_replay(vp_server* s, const vp_job_desc* jobs, const double* arrival_ms, int n,
+                           double timeout_s, vp_job_done* done, double* submit_ms)
+{
+    if (!s || n < 0 || (n > 0 && (!jobs || !arrival_ms || !done)) || !(timeout_s >= 0.0)) return VP_ERR_INVALID_ARG;
+    std::vector<Job> js((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (!(arrival_ms[i] >= 0.0) || !std::isfinite(arrival_ms[i]) || (i > 0 && arrival_ms[i] < arrival_ms[i - 1]))
+            return VP_ERR_INVALID_ARG;
+        const vp_status st = prepare(s, jobs[i], &js[(size_t)i]);
+        if (st != VP_OK) return st;
+    }
+    int64_t first = 0;
+    int got = 0;
+    // moves this replay's finished records to `done` (caller holds the lock)
+    auto collect = [&]() {
+        for (auto it = s->finished.begin(); it != s->finished.end();) {
+            const int64_t i = it->id - first;
+            if (i < 0 || i >= n) {
+                ++it;
+                continue;
+            }
+            done[i] = *it;
+            ++got;
+            it = s->finished.erase(it);
+        }
+    };
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (!s->running.empty() || !s->waiting.empty()) return VP_ERR_INVALID_ARG;
+        const vp_status st = reset_ref(s);
+        if (st != VP_OK) return st;
+        first = s->next_id;
+    }
+    for (int i = 0; i < n; ++i) {
+        for (;;) {
+            std::lock_guard<std::mutex> lock(s->mu);
+            const double now = host_ms(s);
+            if (now >= arrival_ms[i]) {
+                if (submit_ms) submit_ms[i] = now;
+                enqueue_job(s, js[(size_t)i]);
+                collect();
+                break;
+            }
+            progress(s);
+            collect();
+        }
+    }
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            progress(s);
+            collect();
+            if (got == n) break;
+        }
+        if (std::chrono::steady_clock::now() >= t_end) return VP_ERR_TIMEOUT;
+        std::this_thread::yield();
+    }
     return VP_OK;
 }
 
@@ -382,11 +545,7 @@ vp_status vp_server_reset_clock(vp_server* s)
         s->t_ref = std::chrono::steady_clock::now();
         return VP_OK;
     }
-    if (cudaEventRecord(s->ref, s->lanes[0]) != cudaSuccess || cudaEventSynchronize(s->ref) != cudaSuccess) {
-        cudaGetLastError();
-        return VP_ERR_CUDA;
-    }
-    return VP_OK;
+    return reset_ref(s);
 }
 
 vp_status vp_server_get_stats(vp_server* s, vp_server_stats* out)
@@ -414,6 +573,7 @@ vp_status vp_server_destroy(vp_server* s)
         return VP_OK;
     }
     for (cudaStream_t st : s->lanes) cudaStreamSynchronize(st);
+    for (auto& v : s->ranked) destroy_streams(v);
     for (auto& kv : s->jobs) {
         if (kv.second.ev0) cudaEventDestroy(kv.second.ev0);
         if (kv.second.ev1) cudaEventDestroy(kv.second.ev1);

@@ -94,7 +94,7 @@ def test_jobs_same_alone_and_in_the_mix():
     assert st["completed"] == st["submitted"] == len(jobs) and st["queued"] == 0 and st["in_flight"] == 0
     assert 1 < st["max_in_flight"] <= 4
     assert st["pool_high_water"] <= pool and st["pool_used"] == 0
-    for k, (jid, status, t0, t1) in reported.items():
+    for k, (jid, status, t0, t1, rank) in reported.items():
         assert status == 0 and 0.0 <= t0 <= t1, reported[k]
     for jd in jobs:
         mix, alone = jd.outputs(), jd.alone()
@@ -175,3 +175,24 @@ def test_drain_deadline_returns_timeout_then_completes():
     for jd in jobs[:2]:
         for a, b in zip(jd.outputs(), jd.alone()):
             assert np.array_equal(a, b)
+
+
+def test_replay_under_age_priority_same_as_alone():
+    """A trace replayed under VP_SERVE_AGE_PRIORITY (jobs on streams of
+    several priorities, overlapping): every job's outputs equal the plan
+    path's, jobs admitted while others run rank below them, and each job is
+    submitted no earlier than its arrival time."""
+    dev = torch.device("cuda:0")
+    jobs = [JobData(500 + i, SHAPES[i % len(SHAPES)], dev) for i in range(16)]
+    arrival = [0.05 * i for i in range(len(jobs))]
+    with vp.Server(256 << 20, lanes=4) as srv:
+        srv.set_policy(vp.VP_SERVE_AGE_PRIORITY)
+        recs, sub = srv.replay([jd.desc() for jd in jobs], arrival, timeout_s=120.0)
+        st = srv.stats()
+    assert st["completed"] == len(jobs) and st["max_in_flight"] > 1
+    for r, a, s in zip(recs, arrival, sub):
+        assert r[1] == 0 and s >= a and 0.0 <= r[2] <= r[3]
+    assert recs[0][4] == 0 and max(r[4] for r in recs) > 0
+    for jd in jobs:
+        for a, b in zip(jd.outputs(), jd.alone()):
+            assert np.array_equal(a, b), jd.shape

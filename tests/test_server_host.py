@@ -2,7 +2,8 @@
 admission, pool accounting and reporting as the GPU server, jobs running on
 a host clock for C microseconds). No GPU: these cover first-come admission
 by idle lane and pool space, head-of-line waiting, the pool's bookkeeping,
-the drain deadline, and reporting each job once.
+the drain deadline, reporting each job once, the trace replay
+(vp_server_replay) and the age-priority ranks (vp_server_set_policy).
 """
 import time
 
@@ -110,3 +111,64 @@ def test_destroy_with_waiting_jobs():
     for _ in range(3):
         srv.submit(job(10))
     srv.close()
+
+
+def test_replay_submits_at_arrival_times():
+    """vp_server_replay submits each job when the host clock reaches its
+    arrival time, reports every job of the trace in trace order, and leaves
+    nothing for vp_server_poll."""
+    arrivals = [0.0, 0.5, 0.5, 3.0, 3.2, 8.0]          # ms
+    sizes = [1000, 2000, 500, 300, 4000, 700]          # us of fake run time
+    with vp.Server(1 << 30, lanes=2, fake=True) as srv:
+        recs, sub = srv.replay([job(C) for C in sizes], arrivals, timeout_s=20.0)
+        assert [r[0] for r in recs] == sorted(r[0] for r in recs)
+        for a, s, r, C in zip(arrivals, sub, recs, sizes):
+            assert r[1] == 0
+            assert s >= a and s - a < 50.0            # dispatch lag of the replay loop (ms, loose for CI)
+            assert r[2] >= s - 1e-3                     # admitted no earlier than submitted
+            assert r[3] - r[2] == pytest.approx(C * 1e-3, abs=0.5)
+        # two lanes: the third job (arriving with the second) waits for the first to end
+        assert recs[2][2] >= recs[0][3] - 0.2
+        assert srv.poll() == []
+        st = srv.stats()
+        assert st["completed"] == st["submitted"] == len(sizes) and st["in_flight"] == 0
+
+
+def test_replay_refusals_leave_server_untouched():
+    with vp.Server(1 << 30, lanes=2, fake=True) as srv:
+        for arr in ([1.0, 0.5], [-1.0, 0.0], [0.0, float("nan")]):   # decreasing, negative, NaN
+            with pytest.raises(vp.VPError) as e:
+                srv.replay([job(10), job(10)], arr)
+            assert e.value.code == 1
+        with pytest.raises(vp.VPError) as e:                          # one job larger than the pool
+            srv.replay([job(10), job(100000)], [0.0, 0.0])
+        assert e.value.code == 6
+        assert srv.stats()["submitted"] == 0
+        srv.submit(job(20000))                                        # busy server: refused
+        with pytest.raises(vp.VPError) as e:
+            srv.replay([job(10)], [0.0])
+        assert e.value.code == 1
+        drain_all(srv)
+        recs, _ = srv.replay([], [])
+        assert recs == []
+
+
+def test_age_priority_ranks_follow_admission_order():
+    """Under VP_SERVE_AGE_PRIORITY a job admitted while others run takes the
+    rank below the youngest running job's (0 when the server is idle), capped
+    at the lowest of the modelled levels; FCFS reports rank 0."""
+    with vp.Server(1 << 30, lanes=8, fake=True) as srv:
+        recs, _ = srv.replay([job(5000) for _ in range(3)], [0.0, 0.1, 0.2])
+        assert [r[4] for r in recs] == [0, 0, 0]
+        srv.set_policy(vp.VP_SERVE_AGE_PRIORITY)
+        # eight overlapping 5 ms jobs, then one after everything has finished
+        arr = [0.1 * i for i in range(8)] + [40.0]
+        recs, _ = srv.replay([job(5000) for _ in arr], arr)
+        assert [r[4] for r in recs] == [0, 1, 2, 3, 4, 5, 5, 5, 0]
+        srv.submit(job(20000))
+        with pytest.raises(vp.VPError):                 # not while a job runs
+            srv.set_policy(vp.VP_SERVE_FCFS)
+        drain_all(srv)
+        srv.set_policy(vp.VP_SERVE_FCFS)
+        with pytest.raises(vp.VPError):
+            srv.set_policy(2)
