@@ -73,12 +73,14 @@ __device__ __forceinline__ FChan fchan(const FactorArgs& a, int c, int K, int M)
     return f;
 }
 
+constexpr int kRow32 = kMaxK + 1;   // padded row length of the triangular factors in shared memory
+
 template <int MT>
 struct Smem32 {
     float2 refl[kMaxK][MT];    // Householder vector of step t (zero above row t)
     float2 ru[kMaxK][kMaxK];   // ru[t][j]: entry of row t of R' in the column of user j
-    float2 rl[kMaxK][kMaxK];   // R, level order
-    float2 uu[kMaxK][kMaxK];   // U = R^-1, level order
+    float2 rl[kMaxK][kRow32];  // R, level order (rows padded: lane j reading row j hits distinct banks)
+    float2 uu[kMaxK][kRow32];  // U = R^-1, level order (padded likewise)
     float2 phi[kMaxK];         // phase of R'_tt
     float beta[kMaxK];
     float rdiag[kMaxK];        // |R'_tt|
@@ -104,40 +106,66 @@ __device__ __forceinline__ void write_channel_outputs_zero(const FChan& f, int K
     }
 }
 
-// sigma_max(A)^2 of an upper-triangular K x K matrix held in shared memory,
-// by power iteration on A^H A (a lower bound that converges from below). Every
-// lane of the warp calls it; lane j < K holds component j of the iterate.
-__device__ float power_sigma2(const float2 (*A)[kMaxK], int K, int j)
+// sigma_max(A)^2 and sigma_max(B)^2 of two upper-triangular K x K matrices
+// held in shared memory, by power iteration on A^H A and B^H B (lower bounds
+// that converge from below). The two iterations are independent and run
+// interleaved, each with its own operations in its own order. Every lane of
+// the warp calls it; lane j < K holds component j of the iterates; K <= KT.
+template <int KT>
+__device__ void power_sigma2_pair(const float2 (*A)[kRow32], const float2 (*B)[kRow32], int K, int j, float& la,
+                                  float& lb)
 {
     const bool act = j < K;
-    float2 v = make_float2(act ? 1.f + 0.0625f * (float)j : 0.f, 0.f);
-    float lam = 0.f;
+    float2 va = make_float2(act ? 1.f + 0.0625f * (float)j : 0.f, 0.f), vb = va;
+    la = 0.f;
+    lb = 0.f;
     for (int it = 0; it < 6; ++it) {
-        float2 w = make_float2(0.f, 0.f);                       // w = A v
-        for (int k = 0; k < K; ++k) {
-            const float2 vk = make_float2(__shfl_sync(kFull, v.x, k, kLanes), __shfl_sync(kFull, v.y, k, kLanes));
-            if (act && k >= j) w = cfma(A[j][k], vk, w);
+        float2 wa = make_float2(0.f, 0.f), wb = wa;              // w = A v
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if (k < K) {
+                const float2 vak = make_float2(__shfl_sync(kFull, va.x, k, kLanes), __shfl_sync(kFull, va.y, k, kLanes));
+                const float2 vbk = make_float2(__shfl_sync(kFull, vb.x, k, kLanes), __shfl_sync(kFull, vb.y, k, kLanes));
+                if (act && k >= j) {
+                    wa = cfma(A[j][k], vak, wa);
+                    wb = cfma(B[j][k], vbk, wb);
+                }
+            }
         }
-        float2 z = make_float2(0.f, 0.f);                       // z = A^H w
-        for (int i = 0; i < K; ++i) {
-            const float2 wi = make_float2(__shfl_sync(kFull, w.x, i, kLanes), __shfl_sync(kFull, w.y, i, kLanes));
-            if (act && i <= j) z = cfma(make_float2(A[i][j].x, -A[i][j].y), wi, z);
+        float2 za = make_float2(0.f, 0.f), zb = za;              // z = A^H w
+#pragma unroll
+        for (int i = 0; i < KT; ++i) {
+            if (i < K) {
+                const float2 wai = make_float2(__shfl_sync(kFull, wa.x, i, kLanes), __shfl_sync(kFull, wa.y, i, kLanes));
+                const float2 wbi = make_float2(__shfl_sync(kFull, wb.x, i, kLanes), __shfl_sync(kFull, wb.y, i, kLanes));
+                if (act && i <= j) {
+                    za = cfma(make_float2(A[i][j].x, -A[i][j].y), wai, za);
+                    zb = cfma(make_float2(B[i][j].x, -B[i][j].y), wbi, zb);
+                }
+            }
         }
-        float nw = cabs2(w), nv = cabs2(v), nz = cabs2(z);
+        float nwa = cabs2(wa), nva = cabs2(va), nza = cabs2(za);
+        float nwb = cabs2(wb), nvb = cabs2(vb), nzb = cabs2(zb);
 #pragma unroll
         for (int off = 8; off >= 1; off >>= 1) {
-            nw += __shfl_xor_sync(kFull, nw, off, kLanes);
-            nv += __shfl_xor_sync(kFull, nv, off, kLanes);
-            nz += __shfl_xor_sync(kFull, nz, off, kLanes);
+            nwa += __shfl_xor_sync(kFull, nwa, off, kLanes);
+            nva += __shfl_xor_sync(kFull, nva, off, kLanes);
+            nza += __shfl_xor_sync(kFull, nza, off, kLanes);
+            nwb += __shfl_xor_sync(kFull, nwb, off, kLanes);
+            nvb += __shfl_xor_sync(kFull, nvb, off, kLanes);
+            nzb += __shfl_xor_sync(kFull, nzb, off, kLanes);
         }
-        lam = nw / nv;                                          // Rayleigh quotient of A^H A
-        const float sc = rsqrtf(nz);
-        v = make_float2(z.x * sc, z.y * sc);
+        la = nwa / nva;                                          // Rayleigh quotients
+        lb = nwb / nvb;
+        const float sa = rsqrtf(nza), sb = rsqrtf(nzb);
+        va = make_float2(za.x * sa, za.y * sa);
+        vb = make_float2(zb.x * sb, zb.y * sb);
     }
-    return lam;
 }
 
-template <int MT>
+// MT: rows of A (M, or M + K with lambda > 0) rounded up; KT >= K: the
+// unrolled step loops stop at KT, so small K runs a small kernel body.
+template <int MT, int KT>
 __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(FactorArgs a)
 {
     __shared__ Smem32<MT> smem[kChPerBlock32];
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     bool placed = !act;
     bool degenerate = false;
 #pragma unroll
-    for (int t = 0; t < MT; ++t) {
+    for (int t = 0; t < KT; ++t) {
         if (t < K) {
             float nu = 0.f;
 #pragma unroll
@@ -274,7 +302,9 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 
     // cond(H H^H) = (sigma_max(R) sigma_max(U))^2, estimated by power iteration;
     // channels above the plan threshold (or degenerate) go to the FP64 path
-    const float kappa = power_sigma2(sm.rl, K, j) * power_sigma2(sm.uu, K, j);
+    float sr, su;
+    power_sigma2_pair<KT>(sm.rl, sm.uu, K, j, sr, su);
+    const float kappa = sr * su;
     const bool degen = (__ballot_sync(kFull, degenerate) & hmask) != 0u;
     const float thr = (a.probs && valid) ? a.probs[c].kappa_thr : a.kappa_thr;
     const bool to64 = !nonfinite && (degen || !(kappa <= thr));
@@ -320,7 +350,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
         for (int t = 0; t < MT; ++t)
             z[t] = (t < K) ? cmul(sm.phi[t], sm.uu[K - 1 - t][k]) : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = MT - 1; t >= 0; --t) {
+        for (int t = KT - 1; t >= 0; --t) {
             if (t < K) {
                 float2 s = make_float2(0.f, 0.f);
 #pragma unroll
@@ -654,10 +684,16 @@ cudaError_t run_factor32(const FactorArgs& a, cudaStream_t s)
     const int blocks = (a.C + kChPerBlock32 - 1) / kChPerBlock32;
     const int threads = kLanes * kChPerBlock32;
     const int rows = a.lambda > 0.f ? a.M + a.K : a.M;   // rows of A = Hbar^H
-    if (rows <= 4) factor32_kernel<4><<<blocks, threads, 0, s>>>(a);
-    else if (rows <= 8) factor32_kernel<8><<<blocks, threads, 0, s>>>(a);
-    else if (rows <= 16) factor32_kernel<16><<<blocks, threads, 0, s>>>(a);
-    else factor32_kernel<32><<<blocks, threads, 0, s>>>(a);
+    const int kt = a.K <= 4 ? 4 : (a.K <= 8 ? 8 : 16);
+    if (rows <= 4) factor32_kernel<4, 4><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 8 && kt == 4) factor32_kernel<8, 4><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 8) factor32_kernel<8, 8><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 16 && kt == 4) factor32_kernel<16, 4><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 16 && kt == 8) factor32_kernel<16, 8><<<blocks, threads, 0, s>>>(a);
+    else if (rows <= 16) factor32_kernel<16, 16><<<blocks, threads, 0, s>>>(a);
+    else if (kt == 4) factor32_kernel<32, 4><<<blocks, threads, 0, s>>>(a);
+    else if (kt == 8) factor32_kernel<32, 8><<<blocks, threads, 0, s>>>(a);
+    else factor32_kernel<32, 16><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
