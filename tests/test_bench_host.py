@@ -51,3 +51,16 @@ def test_executed_counts_shared_prefixes_once():
 def test_whole_job_rate_and_slowest_rank():
     assert bench.whole_job_rate(2, 1000, 10, 0.5) == 2 * 1000 * 10 / 0.5
     assert bench.max_over_ranks(3.0) == 3.0
+
+
+def test_code_fingerprint_ignores_comments_and_layout(tmp_path, monkeypatch):
+    """A profile stays valid across comment and whitespace edits of the
+    kernel sources, and not across code edits."""
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "k.cu").write_text("int f(int a) {  // add one\n    return a + 1; /* one */\n}\n")
+    base = bench.code_fingerprint(["k.cu"])
+    (tmp_path / "k.cu").write_text("// header\nint f(int a)\n{\n  return a + 1;\n}\n")
+    assert bench.code_fingerprint(["k.cu"]) == base
+    (tmp_path / "k.cu").write_text("int f(int a) { return a + 2; }\n")
+    assert bench.code_fingerprint(["k.cu"]) != base

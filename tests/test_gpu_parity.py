@@ -107,7 +107,7 @@ def test_full_size_sampled(orc, wl):
                   uniform_S=None if wl.per_rb else S)
     C = b.H.shape[0]
     rng = np.random.default_rng(5)
-    chans = np.sort(rng.choice(C, size=min(C, 48), replace=False))
+    chans = np.sort(rng.choice(C, size=min(C, 512), replace=False))
     vecs, off = [], [0]
     for c in chans:
         vv = np.arange(b.vec_off[c], b.vec_off[c + 1])
@@ -275,3 +275,55 @@ def test_maximum_path_budget_16x16(orc, lam):
     ref = orc.precode_batch(H, sym, off, 256, n, lam=lam, nthreads=orc.max_threads())
     assert np.array_equal(gpu["status"] & 3, ref["status"])
     assert_parity(compare(orc, H, sym, off, 256, gpu, ref, lam=lam))
+
+
+def gpu_weights(U):
+    """w_l = U_ll^2 as the FP32 factor forms it (the real diagonal squared in FP32)."""
+    d = np.real(np.diagonal(U, axis1=1, axis2=2)).astype(np.float32)
+    return (d * d).astype(np.float32)
+
+
+@pytest.mark.parametrize("wl,sub", [(W.SMALL_4x4, None), (W.RB_8x8, 24 * 12 + 6), (W.SLOT_16x16, 200)])
+def test_path_lists_bit_exact_on_gpu_weights(orc, wl, sub):
+    """Path selection is integer work once the weights are fixed: on the GPU's
+    own FP32 weights the oracle's MoP K-Best (Eq. mop, per-level children
+    sorted by (metric, code)) must give the GPU's lists, in rank order, on
+    every channel. Checked where both sides' metrics are exact sums: FP32
+    channels (the FP64-flagged ones round w from FP64 and do not expose it)
+    whose weights span less than 2^22, so every FP64 partial sum of
+    w_l * (p_l - 1) is exact (24-bit weights, 3-bit digits, 16 terms) and the
+    GPU's integer scaling keeps every weight."""
+    b = W.make_batch(wl) if sub is None else W.make_batch(wl, subcarriers=sub)
+    gpu = run_gpu(b.H, b.sym, b.vec_off, wl.qam, wl.n_paths)
+    w = gpu_weights(gpu["U"])
+    checked = 0
+    for c in range(b.H.shape[0]):
+        if gpu["status"][c] != 0:
+            continue
+        wc = w[c].astype(np.float64)
+        if not np.all(wc > 0) or wc.max() / wc.min() >= 2.0 ** 22:
+            continue
+        codes, _ = orc.mop_kbest(wc, wl.n_paths)
+        assert np.array_equal(gpu["codes"][c][:len(codes)], codes), c
+        checked += 1
+    print(wl.name, "channels checked", checked, "of", b.H.shape[0])
+    assert checked >= 0.7 * b.H.shape[0]
+
+
+def test_path_lists_bit_exact_full_slot(orc):
+    """The same bit-exact check on 256 channels of the full 16x16 slot launch
+    (the benchmark's configuration)."""
+    b = W.make_batch(W.SLOT_16x16)
+    wl = b.workload
+    gpu = run_gpu(b.H, b.sym, b.vec_off, wl.qam, wl.n_paths, uniform_S=wl.symbols)
+    w = gpu_weights(gpu["U"])
+    rng = np.random.default_rng(11)
+    checked = 0
+    for c in np.sort(rng.choice(b.H.shape[0], size=256, replace=False)):
+        wc = w[c].astype(np.float64)
+        if gpu["status"][c] != 0 or not np.all(wc > 0) or wc.max() / wc.min() >= 2.0 ** 22:
+            continue
+        codes, _ = orc.mop_kbest(wc, wl.n_paths)
+        assert np.array_equal(gpu["codes"][c], codes), c
+        checked += 1
+    assert checked >= 150
