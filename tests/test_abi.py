@@ -219,3 +219,27 @@ def test_batch_tuning_knobs_host_side():
         assert e.value.code == 5
     finally:
         vp.vp_batch_destroy(b)
+
+
+def test_noalloc_capacity_checked_before_any_device_work():
+    """vp_precode_noalloc refuses C > vp_noalloc_max_channels(plan) with
+    VP_ERR_CAPACITY before touching a device, for the plain layout, the
+    lambda > 0 layout (K extra rows of P) and a status-only call (S = 0);
+    C = C_max passes the capacity check (it then needs a device: without
+    one the call fails with VP_ERR_CUDA, never with VP_ERR_CAPACITY)."""
+    import torch
+    lib = vp.load()
+    caps = {}
+    for name, (K, M, q, n, lam) in {"plain": (16, 16, 256, 256, 0.0), "lambda": (16, 16, 256, 256, 0.5),
+                                     "overloaded": (8, 4, 4, 64, 0.5), "small": (4, 4, 16, 16, 0.0)}.items():
+        with vp.Plan(K, M, q, n, lam=lam) as plan:
+            cmax = vp.vp_noalloc_max_channels(plan.handle)
+            caps[name] = cmax
+            assert cmax > 0
+            for S in (14, 0):
+                rc = lib.vp_precode_noalloc(plan.handle, 256, cmax + 1, 256, S, 256, 256, 256, None, None)
+                assert rc == 6, (name, S, rc)
+                if not torch.cuda.is_available():
+                    rc = lib.vp_precode_noalloc(plan.handle, 256, cmax, 256, S, 256, 256, 256, None, None)
+                    assert rc != 6, (name, S, rc)
+    assert caps["lambda"] < caps["plain"] < caps["small"]
