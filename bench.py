@@ -381,9 +381,14 @@ def profiled_traffic(kernel_file: str) -> dict | None:
     if not srcs or fp != fields.get("sources_code_sha256"):
         return None
     try:
-        return {"bytes": float(fields["dram_bytes_per_launch"]), "file": "profiles/" + kernel_file}
+        out = {"bytes": float(fields["dram_bytes_per_launch"]), "file": "profiles/" + kernel_file}
     except (KeyError, ValueError):
         return None
+    try:
+        out["warp_instructions"] = float(fields["warp_instructions_per_launch"])
+    except (KeyError, ValueError):
+        pass
+    return out
 
 
 def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
@@ -1000,6 +1005,14 @@ def run_gpu(args):
                               "path's full descent)",
                 "executed": executed, "executed_frac": executed / peak_tflops,
                 "executed_basis": "the same count with the shared top levels once per distinct prefix, as run"}
+    if tr and "warp_instructions" in tr:
+        # the bound that binds: instruction issue (4 schedulers per SM, one warp instruction each per clock)
+        issue_peak = sms * 4 * sm_mhz * 1e6
+        issue_ach = tr["warp_instructions"] / (search_avg / 1e3)
+        roofline["issue"] = {"achieved": issue_ach / 1e12, "peak": issue_peak / 1e12, "unit": "T warp instr/s",
+                             "frac": issue_ach / issue_peak,
+                             "basis": f"ncu smsp__inst_executed.sum per launch ({tr['file']}) / the live search time; "
+                                      f"peak {sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,

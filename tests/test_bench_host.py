@@ -64,3 +64,20 @@ def test_code_fingerprint_ignores_comments_and_layout(tmp_path, monkeypatch):
     assert bench.code_fingerprint(["k.cu"]) == base
     (tmp_path / "k.cu").write_text("int f(int a) { return a + 2; }\n")
     assert bench.code_fingerprint(["k.cu"]) != base
+
+
+def test_profiled_counters_valid_only_for_the_profiled_code(tmp_path, monkeypatch):
+    """DRAM bytes and warp instructions from a profile summary are used only
+    while the listed sources keep the profiled code fingerprint."""
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "k.cu").write_text("__global__ void k() {}\n")
+    fp = bench.code_fingerprint(["k.cu"])
+    (tmp_path / "profiles" / "p.md").write_text(
+        f"# k\n\n- sources: `k.cu`\n- sources_code_sha256: `{fp}`\n- dram_bytes_per_launch: `1000`\n"
+        "- warp_instructions_per_launch: `5000`\n")
+    got = bench.profiled_traffic("p.md")
+    assert got["bytes"] == 1000.0 and got["warp_instructions"] == 5000.0
+    (tmp_path / "k.cu").write_text("__global__ void k() { int a = 1; }\n")
+    assert bench.profiled_traffic("p.md") is None
