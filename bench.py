@@ -862,10 +862,31 @@ def measure_serving(dev, n_slots: int, lanes: int = 8, pool_mib: int = 1024, n_p
                     "vectors_per_s": V / (end.max() / 1e3), "offered_vectors_per_s": V / (arr[-1] / 1e3),
                     "capacity_vectors_per_s": cap, "outputs_checked": checked,
                     "max_in_flight": st["max_in_flight"], "pool_high_water_mib": st["pool_high_water"] / 2**20})
+        if load == loads[0]:
+            # each job type alone (arrivals 3 ms apart, after a warm-up): the floor of its latency
+            alone = {}
+            for n in n_paths:
+                types = sorted(sets)
+                descs = []
+                for t in types:
+                    H, sym, x, l, g = sets[t][0]
+                    descs.append(vp.job_desc(t[0], t[1], t[2], n, H.shape[0], sym.shape[0] // H.shape[0],
+                                             H, sym, x, l, g))
+                with vp.Server(pool_mib << 20, lanes) as srv:
+                    srv.replay(descs, [0.0] * len(descs))
+                    recs, sub = srv.replay(descs * 3, [3.0 * i for i in range(3 * len(descs))], timeout_s=60.0)
+                for i, t in enumerate(types):
+                    ms = sorted(recs[i + k * len(types)][3] - sub[i + k * len(types)] for k in range(3))
+                    alone[f"n{n}_K{t[0]}_Q{t[2]}"] = ms[1]
+            out["alone_job_ms"] = alone
         out["inputs"] = (f"{ring} independent draws per job type with their own outputs "
                          f"({sum(t[0].numel() * 8 + t[1].numel() for v in sets.values() for t in v) / 2**20:.0f} MiB "
                          "of H and symbols at the last load)")
         del sets
+    for n in n_paths:
+        ok = [r["jobs_per_slot"] for r in out["runs"]
+              if r["n_paths"] == n and r["policy"] == "fcfs" and r["p99_job_ms"] <= out["deadline_ms"]]
+        out[f"max_load_p99_within_deadline_n{n}"] = max(ok) if ok else None
     return out
 
 
