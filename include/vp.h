@@ -430,7 +430,13 @@ size_t vp_precode_batch_workspace_bytes(const vp_problem_desc* descs, int n_prob
  * Time. Job times are device times in milliseconds since the last
  * vp_server_reset_clock (one event on lane 0, waited for by the host before
  * that call returns), from the events recorded on the job's lane before its
- * first and after its last kernel.
+ * first and after its last kernel. The same call zeroes a host clock when the
+ * wait returns (used by vp_server_replay and by the fake server), so host
+ * times read at most that wait's latency behind device times.
+ *
+ * The server serves the paper's per-slot precoding (Alg. 2 on every
+ * subcarrier of a slot) for several cells or slots whose jobs arrive
+ * independently; the paper's accelerator processes one stream of slots.
  */
 typedef struct vp_server vp_server;
 
