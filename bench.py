@@ -394,10 +394,11 @@ def profiled_traffic(kernel_file: str) -> dict | None:
 def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
     """Uneven batch: 20,000 problems x 14 vectors, (K x M, Q, n) uniform over
     {4x8, 8x16, 12x16, 16x16} x {16, 64, 256} x {16, 64, 256, 1024}. The
-    search as one launch per K tile (the default; also captured in a CUDA
-    graph and autotuned), in one persistent launch (direct and autotuned),
-    and the plain path (one vp_factorize + vp_precode per problem, one plan
-    per distinct shape)."""
+    search as one launch per K tile with each stage's launches side by side
+    (the default; also captured in a CUDA graph and autotuned), the same
+    launches in order on one stream, the search in one persistent launch
+    (direct and autotuned), and the plain path (one vp_factorize +
+    vp_precode per problem, one plan per distinct shape)."""
     import numpy as np
     import torch
 
@@ -442,8 +443,17 @@ def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
         out["persistent_tuned_knob"] = b.autotune(reps=3, cache="", stream=stream)[-1]
         ms = timed(lambda: b.launch(stream), 10)
         out["persistent_tuned_ms"] = ms
-    # the search as one launch per K tile (the default); direct, in a CUDA
-    # graph, and autotuned
+    # every launch in order on one stream (the stages' groups not side by side)
+    with vp.Batch(descs, stream=stream, concurrent=0) as b:
+        for _ in range(3):
+            b.launch(stream)
+        torch.cuda.synchronize()
+        ms = timed(lambda: b.launch(stream), 10)
+        out["in_order_ms"] = ms
+        out["in_order_vectors_per_s"] = V / (ms / 1e3)
+    # the search as one launch per K tile and each stage's launches side by
+    # side on the batch's streams (the default); direct, in a CUDA graph, and
+    # autotuned
     with vp.Batch(descs, stream=stream) as b:
         for _ in range(3):
             b.launch(stream)

@@ -346,6 +346,22 @@ int vp_batch_launch_count(const vp_batch* batch);
 vp_status vp_batch_set_persistent(vp_batch* batch, int persistent);
 
 /*
+ * Whether the launches of one stage (the factor launches per (K, M), the
+ * path-selection launches per path class, the search launches per K tile)
+ * run side by side: 1 (the default for a handle made by vp_batch_create)
+ * puts group k > 0 of a stage on the batch's side stream k - 1, forked from
+ * the caller's stream by an event and joined back before the next stage
+ * (the groups touch disjoint problems; a CUDA graph capture of
+ * vp_batch_launch takes the fork and join along); 0 enqueues every launch on
+ * the caller's stream in order. The side streams (4) and their events are
+ * created by vp_batch_bind on the current device and freed by
+ * vp_batch_destroy; the outputs are the same either way. vp_precode_batch
+ * uses 0. VP_ERR_INVALID_ARG for other values; VP_ERR_CUDA if the streams
+ * cannot be created.
+ */
+vp_status vp_batch_set_concurrent(vp_batch* batch, int concurrent);
+
+/*
  * Autotuner. Every path-selection and search launch of a batch (a "group")
  * has one mapping knob (0 is the built-in choice):
  *   path selection: the threads that work on one channel's path lists

@@ -32,7 +32,7 @@ __all__ = [
     "vp_server_drain", "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "Server",
     "vp_batch_autotune", "vp_batch_get_tuning", "vp_batch_set_tuning", "vp_batch_group_info",
     "vp_server_create_fake", "vp_batch_set_persistent", "EXPORTED_SYMBOLS", "Plan",
-    "vp_server_set_policy", "vp_server_replay", "VP_SERVE_FCFS", "VP_SERVE_AGE_PRIORITY",
+    "vp_server_set_policy", "vp_server_replay", "VP_SERVE_FCFS", "VP_SERVE_AGE_PRIORITY", "vp_batch_set_concurrent",
 ]
 
 VP_CH_NONFINITE = 1
@@ -61,7 +61,7 @@ EXPORTED_SYMBOLS = (
     "vp_precode_batch_workspace_bytes", "vp_server_create", "vp_server_submit", "vp_server_poll", "vp_server_drain",
     "vp_server_reset_clock", "vp_server_get_stats", "vp_server_destroy", "vp_batch_autotune", "vp_batch_get_tuning",
     "vp_batch_set_tuning", "vp_batch_group_info", "vp_server_create_fake", "vp_batch_set_persistent",
-    "vp_server_set_policy", "vp_server_replay",
+    "vp_server_set_policy", "vp_server_replay", "vp_batch_set_concurrent",
 )
 
 
@@ -148,6 +148,8 @@ def load():
             L.vp_batch_launch.argtypes = [vpp, vpp]
             L.vp_batch_set_persistent.argtypes = [vpp, ctypes.c_int]
             L.vp_batch_set_persistent.restype = ctypes.c_int
+            L.vp_batch_set_concurrent.argtypes = [vpp, ctypes.c_int]
+            L.vp_batch_set_concurrent.restype = ctypes.c_int
             L.vp_batch_launch_count.argtypes = [vpp]
             L.vp_batch_launch_count.restype = ctypes.c_int
             L.vp_batch_destroy.argtypes = [vpp]
@@ -372,12 +374,14 @@ def packed_descs(pk, H, sym, x, l, gamma, status=None, tau=0.0):
 class Batch:
     """Owning handle of a vp_batch and its device workspace (a torch uint8 tensor)."""
 
-    def __init__(self, descs, fp64_threshold: float = 1e4, stream=None, persistent: int = 0):
+    def __init__(self, descs, fp64_threshold: float = 1e4, stream=None, persistent: int = 0, concurrent: int = 1):
         import torch
         self.descs = _desc_array(descs)
         self.handle = vp_batch_create(self.descs, fp64_threshold)
         if persistent:
             vp_batch_set_persistent(self.handle, persistent)
+        if not concurrent:
+            vp_batch_set_concurrent(self.handle, 0)
         nbytes = vp_batch_workspace_bytes(self.handle)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.workspace.data_ptr()
@@ -433,6 +437,10 @@ class Batch:
 
 def vp_batch_set_persistent(batch: int, persistent: int) -> None:
     _check(load().vp_batch_set_persistent(batch, int(persistent)), "vp_batch_set_persistent")
+
+
+def vp_batch_set_concurrent(batch: int, concurrent: int) -> None:
+    _check(load().vp_batch_set_concurrent(batch, int(concurrent)), "vp_batch_set_concurrent")
 
 
 def vp_batch_autotune(batch: int, reps: int = 3, stream=None) -> None:

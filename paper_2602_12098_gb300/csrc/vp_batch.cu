@@ -9,7 +9,9 @@
 // per K <= 2, 4, 8, 12, 16. Inside a launch the problems run heaviest first
 // (S * n * K^2), so the long blocks start early and the short ones fill the
 // tail. The FP64 fix-up runs once over the channels all factor launches
-// flagged.
+// flagged. The launches of one stage touch disjoint problems, so by default
+// they run side by side on the batch's own streams (the latency-bound factor
+// launches and the launch tails overlap), each stage joined before the next.
 //
 // Workspace (caller-owned device memory): the problem table, the three
 // launch orders, the FP64 list and every problem's resident state.
@@ -41,6 +43,13 @@ struct vp_batch {
     // first, all K tiles: the stage-3 group), or one launch per K tile (the
     // default: faster on GB300 for the 20,000-problem mix, 4.82 vs 5.05 ms)
     int persistent = 0;
+    // the launches of one stage (they touch disjoint problems) run side by
+    // side: group k > 0 of a stage on side stream k - 1, forked from and
+    // joined back to the caller's stream by events (graph-capturable); off,
+    // every launch goes to the caller's stream in order
+    int concurrent = 1;
+    std::vector<cudaStream_t> side;        // created by vp_batch_bind
+    std::vector<cudaEvent_t> joins;        // one per side stream, plus the fork event last
     int km_all = 0, n_all = 0, s_all = 0;
     size_t off_table = 0, off_ids = 0, off_nflag = 0, off_flags = 0, off_state = 0, bytes = 0;
     unsigned char* ws = nullptr;
@@ -223,6 +232,60 @@ void fill_table(vp_batch* b)
     }
 }
 
+constexpr int kSideStreams = 4;
+
+// Streams and events of the concurrent mode, created once (at bind, before
+// any stream capture) on the current device.
+bool make_side_streams(vp_batch* b)
+{
+    if (!b->side.empty()) return true;
+    for (int i = 0; i < kSideStreams; ++i) {
+        cudaStream_t q = nullptr;
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) break;
+        b->side.push_back(q);
+    }
+    for (int i = 0; (int)b->side.size() == kSideStreams && i <= kSideStreams; ++i) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
+        b->joins.push_back(e);
+    }
+    if ((int)b->side.size() == kSideStreams && (int)b->joins.size() == kSideStreams + 1) return true;
+    cudaGetLastError();
+    for (cudaStream_t q : b->side) cudaStreamDestroy(q);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    b->side.clear();
+    b->joins.clear();
+    return false;
+}
+
+// Launches every group of one stage: in order on `s`, or (concurrent mode)
+// the k-th group on side stream k - 1 after a fork event on `s`, then `s`
+// waits for every side stream it used.
+template <class F>
+cudaError_t launch_stage(const vp_batch* b, int stage, cudaStream_t s, F&& launch)
+{
+    const bool conc = b->concurrent && !b->side.empty();
+    cudaEvent_t fork = conc ? b->joins[kSideStreams] : nullptr;
+    int k = 0;
+    cudaError_t e = cudaSuccess;
+    for (const vp_batch::Group& g : b->groups) {
+        if (g.stage != stage) continue;
+        cudaStream_t q = s;
+        if (conc && k > 0) {
+            q = b->side[(k - 1) % kSideStreams];
+            if (k == 1 && (e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+            if (k <= kSideStreams && (e = cudaStreamWaitEvent(q, fork, 0)) != cudaSuccess) return e;
+        }
+        if ((e = launch(g, q)) != cudaSuccess) return e;
+        ++k;
+    }
+    for (int i = 0; conc && i < k - 1 && i < kSideStreams; ++i) {
+        if ((e = cudaEventRecord(b->joins[i], b->side[i])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, b->joins[i], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // One search group: a K tile's launch (stage 2), or the persistent launch of
 // every problem (stage 3, its counter reset first).
 cudaError_t launch_search_group(const vp_batch* b, const vp_batch::Group& g, cudaStream_t s)
@@ -278,6 +341,7 @@ vp_status vp_batch_bind(vp_batch* b, void* workspace, size_t workspace_bytes, vo
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t N = b->descs.size();
+    if (b->concurrent && !make_side_streams(b)) b->concurrent = 0;   // no side streams: one stream in order
     if (cudaMemcpyAsync(b->ws + b->off_table, b->table.data(), sizeof(vp::BatchProblem) * N, cudaMemcpyHostToDevice,
                         s) != cudaSuccess ||
         cudaMemcpyAsync(b->ws + b->off_ids, b->ids.data(), sizeof(int) * 4 * N, cudaMemcpyHostToDevice, s) !=
@@ -299,17 +363,19 @@ vp_status vp_batch_launch(vp_batch* b, void* stream)
     int* nflag = reinterpret_cast<int*>(b->ws + b->off_nflag);
     int* flags = reinterpret_cast<int*>(b->ws + b->off_flags);
     if (cudaMemsetAsync(nflag, 0, sizeof(int), s) != cudaSuccess) return VP_ERR_CUDA;
-    for (const vp_batch::Group& g : b->groups)
-        if (g.stage == 0 &&
-            vp::launch_factor32_batch(probs, ids + g.start, g.count, g.K, g.M, nflag, flags, s) != cudaSuccess)
-            return VP_ERR_CUDA;
+    if (launch_stage(b, 0, s, [&](const vp_batch::Group& g, cudaStream_t q) {
+            return vp::launch_factor32_batch(probs, ids + g.start, g.count, g.K, g.M, nflag, flags, q);
+        }) != cudaSuccess)
+        return VP_ERR_CUDA;
     if (vp::launch_factor64_batch(probs, nflag, flags, N, s) != cudaSuccess) return VP_ERR_CUDA;
-    for (const vp_batch::Group& g : b->groups)
-        if (g.stage == 1 && vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, s, g.knob) !=
-                                cudaSuccess)
-            return VP_ERR_CUDA;
-    for (const vp_batch::Group& g : b->groups)
-        if (g.stage == (b->persistent ? 3 : 2) && launch_search_group(b, g, s) != cudaSuccess) return VP_ERR_CUDA;
+    if (launch_stage(b, 1, s, [&](const vp_batch::Group& g, cudaStream_t q) {
+            return vp::launch_pathsel_batch(probs, ids + N + g.start, g.count, g.n_max, q, g.knob);
+        }) != cudaSuccess)
+        return VP_ERR_CUDA;
+    if (launch_stage(b, b->persistent ? 3 : 2, s, [&](const vp_batch::Group& g, cudaStream_t q) {
+            return launch_search_group(b, g, q);
+        }) != cudaSuccess)
+        return VP_ERR_CUDA;
     return VP_OK;
 }
 
@@ -317,6 +383,14 @@ vp_status vp_batch_set_persistent(vp_batch* b, int persistent)
 {
     if (!b || (persistent != 0 && persistent != 1)) return VP_ERR_INVALID_ARG;
     b->persistent = persistent;
+    return VP_OK;
+}
+
+vp_status vp_batch_set_concurrent(vp_batch* b, int concurrent)
+{
+    if (!b || (concurrent != 0 && concurrent != 1)) return VP_ERR_INVALID_ARG;
+    if (concurrent && b->ws && !make_side_streams(b)) return VP_ERR_CUDA;
+    b->concurrent = concurrent;
     return VP_OK;
 }
 
@@ -438,6 +512,13 @@ int vp_batch_launch_count(const vp_batch* b)
 
 vp_status vp_batch_destroy(vp_batch* b)
 {
+    if (!b) return VP_OK;
+    for (cudaStream_t q : b->side) {
+        cudaStreamSynchronize(q);
+        cudaStreamDestroy(q);
+    }
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    cudaGetLastError();
     delete b;
     return VP_OK;
 }
@@ -457,6 +538,7 @@ vp_status vp_precode_batch(const vp_problem_desc* descs, int n_problems, size_t 
     vp_batch* b = nullptr;
     vp_status st = vp_batch_create(descs, n_problems, 1e4f, &b);
     if (st != VP_OK) return st;
+    b->concurrent = 0;   // one call, one stream: no side streams to create per call
     st = vp_batch_bind(b, workspace, workspace_bytes, stream);
     if (st == VP_OK) st = vp_batch_launch(b, stream);
     vp_batch_destroy(b);

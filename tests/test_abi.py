@@ -94,6 +94,13 @@ def test_batch_validation_and_grouping():
         vp.vp_batch_set_persistent(b, 0)
         with pytest.raises(vp.VPError):
             vp.vp_batch_set_persistent(b, 2)
+        for bad in (2, -1):
+            with pytest.raises(vp.VPError) as e:
+                vp.vp_batch_set_concurrent(b, bad)
+            assert e.value.code == 1
+        vp.vp_batch_set_concurrent(b, 0)                 # unbound: no streams needed either way
+        vp.vp_batch_set_concurrent(b, 1)
+        assert vp.vp_batch_launch_count(b) == 4 + 4 + 4 + 1
         info = vp.vp_batch_group_info(b)
         assert [g[0] for g in info] == [0] * 4 + [1] * 4 + [2] * 4 + [3]
         assert info[-1][1] == len(good) and info[-1][4] == 1024 and info[-1][5] == 14

@@ -243,3 +243,32 @@ def test_persistent_search_equals_grouped_launches():
             got.fetch()
         assert np.array_equal(ref.x_np, got.x_np) and np.array_equal(ref.l_np, got.l_np)
         assert np.array_equal(ref.g_np, got.g_np) and np.array_equal(ref.st_np, got.st_np)
+
+
+def test_concurrent_stages_equal_in_order_launches():
+    """The launches of a stage run side by side by default (the batch's side
+    streams); the outputs equal those of the in-order launches on one stream,
+    directly and through a CUDA graph capture."""
+    probs = mixed_problems(60, 5)
+    outs = []
+    for conc in (0, 1):
+        pkd = Packed(probs)
+        stream = torch.cuda.Stream()
+        with vp.Batch(pkd.descs, stream=stream, concurrent=conc) as b:
+            with torch.cuda.stream(stream):
+                b.launch(stream)
+            torch.cuda.synchronize()
+            outs.append([t.cpu().numpy().copy() for t in (pkd.x, pkd.l, pkd.g)])
+            if conc:
+                for t in (pkd.x, pkd.l, pkd.g):
+                    t.zero_()
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    b.launch(stream)
+                g.replay()
+                torch.cuda.synchronize()
+                outs.append([t.cpu().numpy().copy() for t in (pkd.x, pkd.l, pkd.g)])
+    for other in outs[1:]:
+        for a, c in zip(outs[0], other):
+            assert np.array_equal(a, c, equal_nan=a.dtype.kind in "fc")
