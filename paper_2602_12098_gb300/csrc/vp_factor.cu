@@ -380,14 +380,20 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 }
 
 // ---------------------------------------------------------------------------
-// FP64 path for the flagged channels: one warp per channel, lanes strided over
-// the entries of each (triangular) matrix operation. GB300 issues FP64 FMAs
+// FP64 path for the flagged channels: a block of NT threads per channel,
+// strided over the entries of each (triangular) matrix operation. GB300 issues FP64 FMAs
 // at 1/64 of the FP32 rate, so FP64 is kept to the pivoted Cholesky of the
 // Gram matrix, U = R^-1 and one Newton step, with the lanes of every FP64
 // instruction packed; the Gram matrix, A = U2^H U2 and P = H^H A are
 // accumulated in compensated FP32 (exact products, ~48-bit sums).
 
-constexpr int kW64 = 1;   // channels (warps) per block (27 KB of shared memory each)
+// Threads on one flagged channel (one channel per block, 27 KB of shared
+// memory): two warps split every entry loop; the small reductions (largest
+// diagonal, pivot) run on each warp over the same shared values. Measured on
+// GB300 (outputs identical for 1, 2 and 4 warps): 2 warps cut vp_factorize
+// by 8 us on the Kronecker 16x16 slot (625 flagged channels) and by 14 us on
+// an i.i.d. 16x16 slot (252); 4 warps gained nothing more.
+constexpr int kNT64 = 64;
 
 struct Smem64 {
     float2 h[kMaxK][kMaxM];      // H rows (user order)
@@ -427,25 +433,28 @@ __device__ __forceinline__ void cdot2(float2 x, float2 yh, float2 yl, float& re,
     ime = fmaf(x.x, yl.y, fmaf(x.y, yl.x, ime));
 }
 
-__global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
+// One flagged channel per block (grid-stride over the flag list); every
+// thread runs the same control flow, so the block barriers are uniform.
+template <int NT>
+__global__ void __launch_bounds__(NT) factor64_kernel(FactorArgs a)
 {
-    __shared__ Smem64 smem[kW64];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Smem64& sm = smem[warp];
+    __shared__ Smem64 sm;
+    const int tid = threadIdx.x, lane = threadIdx.x & 31;
     const int nflag = *a.nflag_in;
+    auto gsync = [&]() { if (NT == 32) __syncwarp(); else __syncthreads(); };
 
-    for (int slot = blockIdx.x * kW64 + warp; slot < nflag; slot += gridDim.x * kW64) {
+    for (int slot = blockIdx.x; slot < nflag; slot += gridDim.x) {
         const int c = a.flags[slot];
         const int K = a.probs ? a.probs[c].K : a.K;
         const int M = a.probs ? a.probs[c].M : a.M;
         const int Mp = a.probs ? M : a.Mp;
         const float lam = a.probs ? 0.f : a.lambda;
         const FChan f = fchan(a, c, K, M);
-        for (int i = lane; i < K * M; i += 32) sm.h[i / M][i % M] = f.H[i];
-        if (lane < K) sm.rem[lane] = lane;
-        __syncwarp();
+        for (int i = tid; i < K * M; i += NT) sm.h[i / M][i % M] = f.H[i];
+        if (tid < K) sm.rem[tid] = tid;
+        gsync();
         // Gram matrix (compensated FP32, exact for FP32 input), both triangles in FP64
-        for (int e = lane; e < K * (K + 1) / 2; e += 32) {
+        for (int e = tid; e < K * (K + 1) / 2; e += NT) {
             int r, q;
             tri_index(e, r, q);
             float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
@@ -461,7 +470,7 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
             sm.s[r][q] = g;
             sm.s[q][r] = zconj(g);
         }
-        __syncwarp();
+        gsync();
         double dmax = lane < K ? sm.s[lane][lane].x : 0.0;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
@@ -499,22 +508,22 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
             const double rt = key * irt;
             // remove p from the remaining list (move the last one into its position)
             const int last = sm.rem[m - 1];
-            __syncwarp();
-            if (lane == 0) {
+            gsync();
+            if (tid == 0) {
                 sm.rem[kp] = last;
                 sm.rd[t] = rt;
                 sm.rinv[t] = irt;
                 sm.uol[t] = p;
             }
-            __syncwarp();
-            if (lane < m - 1) {
-                const double2 v = sm.s[sm.rem[lane]][p];
+            gsync();
+            if (tid < m - 1) {
+                const double2 v = sm.s[sm.rem[tid]][p];
                 const double2 l = make_double2(v.x * irt, v.y * irt);
-                sm.pc[lane] = l;
-                sm.lc[t][sm.rem[lane]] = l;
+                sm.pc[tid] = l;
+                sm.lc[t][sm.rem[tid]] = l;
             }
-            __syncwarp();
-            for (int e = lane; e < (m - 1) * m / 2; e += 32) {        // Schur update, packed lower triangle
+            gsync();
+            for (int e = tid; e < (m - 1) * m / 2; e += NT) {        // Schur update, packed lower triangle
                 int ia, ib;
                 tri_index(e, ia, ib);
                 const int ua = sm.rem[ia], ub = sm.rem[ib];
@@ -523,64 +532,64 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 sm.s[ua][ub] = v;
                 sm.s[ub][ua] = zconj(v);
             }
-            __syncwarp();
+            gsync();
         }
 
         if (!singular) {
-            for (int e = lane; e < K * K; e += 32) {                    // R in level order
+            for (int e = tid; e < K * K; e += NT) {                    // R in level order
                 const int r = e / K, q = e % K;
                 sm.r[r][q] = (q > r) ? sm.lc[q][sm.uol[r]] : (q == r ? make_double2(sm.rd[r], 0.0) : make_double2(0.0, 0.0));
             }
-            __syncwarp();
-            for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = make_double2(0.0, 0.0);
-            __syncwarp();
+            gsync();
+            for (int e = tid; e < K * K; e += NT) sm.lc[e / K][e % K] = make_double2(0.0, 0.0);
+            gsync();
             // U = R^-1 by rows from the bottom: U_m. = (e_m - sum_{j>m} R_mj U_j.) / R_mm
             for (int m = K - 1; m >= 0; --m) {
-                if (lane < K) {
-                    const int k = lane;
+                if (tid < K) {
+                    const int k = tid;
                     const double2 acc = sm.lc[m][k];
                     const double ri = sm.rinv[m];
                     sm.u[m][k] = (k < m) ? make_double2(0.0, 0.0)
                                          : make_double2(((k == m ? 1.0 : 0.0) - acc.x) * ri, -acc.y * ri);
                 }
-                __syncwarp();
+                gsync();
                 const int w = K - m;                                    // entries (i < m, k >= m)
-                for (int e = lane; e < m * w; e += 32) {
+                for (int e = tid; e < m * w; e += NT) {
                     const int i = e / w, k = m + e % w;
                     sm.lc[i][k] = zfma(sm.r[i][m], sm.u[m][k], sm.lc[i][k]);
                 }
-                __syncwarp();
+                gsync();
             }
             // one Newton step: E = I - R U, U2 = U + U E (both upper triangular), accumulated by rank-1 steps
-            for (int e = lane; e < K * K; e += 32) {
+            for (int e = tid; e < K * K; e += NT) {
                 const int r = e / K, q = e % K;
                 sm.s[r][q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
             }
-            __syncwarp();
+            gsync();
             for (int m = 0; m < K; ++m) {                               // E_ik -= R_im U_mk, i <= m <= k
                 const int w = K - m;
-                for (int e = lane; e < (m + 1) * w; e += 32) {
+                for (int e = tid; e < (m + 1) * w; e += NT) {
                     const int i = e / w, k = m + e % w;
                     const double2 pr = zmul(sm.r[i][m], sm.u[m][k]);
                     sm.s[i][k].x -= pr.x;
                     sm.s[i][k].y -= pr.y;
                 }
-                __syncwarp();
+                gsync();
             }
-            for (int e = lane; e < K * K; e += 32) sm.lc[e / K][e % K] = sm.u[e / K][e % K];
-            __syncwarp();
+            for (int e = tid; e < K * K; e += NT) sm.lc[e / K][e % K] = sm.u[e / K][e % K];
+            gsync();
             for (int m = 0; m < K; ++m) {                               // U2_ik += U_im E_mk, i <= m <= k
                 const int w = K - m;
-                for (int e = lane; e < (m + 1) * w; e += 32) {
+                for (int e = tid; e < (m + 1) * w; e += NT) {
                     const int i = e / w, k = m + e % w;
                     sm.lc[i][k] = zfma(sm.u[i][m], sm.s[m][k], sm.lc[i][k]);
                 }
-                __syncwarp();
+                gsync();
             }
             // U2 (in lc) as FP32 hi + lo; outputs: row r of U~, w_r, user of level r
-            if (lane < K) sm.rd[lane] = 1.0 / sm.lc[lane][lane].x;     // 1 / U2_rr
-            __syncwarp();
-            for (int e = lane; e < K * K; e += 32) {
+            if (tid < K) sm.rd[tid] = 1.0 / sm.lc[tid][tid].x;     // 1 / U2_rr
+            gsync();
+            for (int e = tid; e < K * K; e += NT) {
                 const int r = e / K, q = e % K;
                 const double2 v = sm.lc[r][q];
                 const float hx = (float)v.x, hy = (float)v.y;
@@ -598,9 +607,9 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                     if (f.ul_out) f.ul_out[r] = (uint8_t)sm.uol[r];
                 }
             }
-            __syncwarp();
+            gsync();
             // A = U2^H U2 (Hermitian) in compensated FP32: A_ik = sum_{m <= min(i,k)} conj(U2_mi) U2_mk
-            for (int e = lane; e < K * (K + 1) / 2; e += 32) {
+            for (int e = tid; e < K * (K + 1) / 2; e += NT) {
                 int i, k;
                 tri_index(e, i, k);                                     // i >= k
                 float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
@@ -618,9 +627,9 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 sm.ahi[k][i] = make_float2(hi.x, -hi.y);
                 sm.alo[k][i] = make_float2(lo.x, -lo.y);
             }
-            __syncwarp();
+            gsync();
             // P_level[m][k] = sum_j conj(H_perm[j][m]) A[j][k], compensated FP32
-            for (int e = lane; e < M * K; e += 32) {
+            for (int e = tid; e < M * K; e += NT) {
                 const int m = e / K, k = e % K;
                 float re = 0.f, ree = 0.f, im = 0.f, ime = 0.f;
                 for (int j = 0; j < K; ++j) {
@@ -635,7 +644,7 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 if (f.P_out) f.P_out[m * K + uk] = hi;
             }
             // regularisation rows (lambda > 0): row M + u of P is lambda A[level of u][.]
-            for (int e = lane; e < (Mp - M) * K; e += 32) {
+            for (int e = tid; e < (Mp - M) * K; e += NT) {
                 const int u = e / K, k = e % K;
                 int lu = 0;
                 for (int i = 0; i < K; ++i) lu = (sm.uol[i] == u) ? i : lu;
@@ -647,12 +656,12 @@ __global__ void __launch_bounds__(32 * kW64) factor64_kernel(FactorArgs a)
                 f.s.pt[uk * Mp + M + u] = make_float2(hx, hy);
                 f.s.ptlo[uk * Mp + M + u] = make_float2(fmaf(lam, al.x, ex), fmaf(lam, al.y, ey));
             }
-            if (lane == 0) f.s.st[0] = (uint8_t)VP_CH_FP64;
+            if (tid == 0) f.s.st[0] = (uint8_t)VP_CH_FP64;
         } else {
-            if (lane < 16) write_channel_outputs_zero(f, K, M, Mp, lane);
-            if (lane == 0) f.s.st[0] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
+            if (tid < 16) write_channel_outputs_zero(f, K, M, Mp, tid);
+            if (tid == 0) f.s.st[0] = (uint8_t)(VP_CH_FP64 | VP_CH_SINGULAR);
         }
-        __syncwarp();
+        gsync();
     }
 }
 
@@ -699,10 +708,10 @@ cudaError_t run_factor32(const FactorArgs& a, cudaStream_t s)
 
 cudaError_t run_factor64(const FactorArgs& a, int max_flagged, cudaStream_t s)
 {
-    int blocks = (max_flagged + kW64 - 1) / kW64;
+    int blocks = max_flagged;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    factor64_kernel<<<blocks, 32 * kW64, 0, s>>>(a);
+    factor64_kernel<kNT64><<<blocks, kNT64, 0, s>>>(a);
     return cudaGetLastError();
 }
 
