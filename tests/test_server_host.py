@@ -172,3 +172,41 @@ def test_age_priority_ranks_follow_admission_order():
         srv.set_policy(vp.VP_SERVE_FCFS)
         with pytest.raises(vp.VPError):
             srv.set_policy(2)
+
+
+def test_replay_invariants_random_traces():
+    """Random traces on the fake server (sizes, arrivals, lanes, pool): every
+    job is reported once and in trace order; admission is first come, first
+    served (admission times never decrease along the trace); a job never
+    starts before it was submitted; its run lasts its C microseconds; the
+    server never runs more jobs than lanes, nor uses more pool than it has."""
+    import random
+    unit = per_channel_bytes()
+    rng = random.Random(2602)
+    for trial in range(6):
+        lanes = rng.choice([1, 2, 3, 5])
+        pool = (rng.choice([3000, 6000, 20000]) * unit) + (1 << 20)
+        n = rng.randint(5, 25)
+        sizes = [rng.randint(50, 2500) for _ in range(n)]
+        arr, t = [], 0.0
+        for _ in range(n):
+            t += rng.choice([0.0, 0.05, 0.3, 1.0])
+            arr.append(round(t, 3))
+        with vp.Server(pool, lanes=lanes, fake=True) as srv:
+            recs, sub = srv.replay([job(C) for C in sizes], arr, timeout_s=30.0)
+            st = srv.stats()
+        assert [r[0] for r in recs] == list(range(recs[0][0], recs[0][0] + n))
+        assert all(r[1] == 0 for r in recs)
+        admits = [r[2] for r in recs]
+        assert all(b >= a - 0.05 for a, b in zip(admits, admits[1:])), (trial, admits)
+        for r, s_ms, C in zip(recs, sub, sizes):
+            assert r[2] >= s_ms - 1e-3
+            assert r[3] - r[2] == pytest.approx(C * 1e-3, abs=0.5)
+        assert 1 <= st["max_in_flight"] <= lanes
+        assert st["pool_high_water"] <= pool and st["pool_used"] == 0
+        # at any instant at most `lanes` jobs ran
+        events = sorted([(r[2], 1) for r in recs] + [(r[3], -1) for r in recs], key=lambda e: (e[0], e[1]))
+        live = 0
+        for _, d in events:
+            live += d
+            assert live <= lanes
