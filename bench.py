@@ -443,6 +443,18 @@ def measure_batched(dev, flush, symbols_per_problem: int = 14) -> dict:
         out["persistent_tuned_knob"] = b.autotune(reps=3, cache="", stream=stream)[-1]
         ms = timed(lambda: b.launch(stream), 10)
         out["persistent_tuned_ms"] = ms
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            b.launch(stream)
+
+        def replay_p():
+            with torch.cuda.stream(stream):
+                graph.replay()
+
+        for _ in range(3):
+            replay_p()
+        out["persistent_graph_ms"] = timed(replay_p, 10)
+        del graph
     # every launch in order on one stream (the stages' groups not side by side)
     with vp.Batch(descs, stream=stream, concurrent=0) as b:
         for _ in range(3):
