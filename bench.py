@@ -265,7 +265,7 @@ def oracle_configs(configs_sample: dict, threads: int) -> dict:
     return out
 
 
-def cpu_baseline(w, budget_s: float = 10.0, gpu_sample=None, configs_sample=None) -> dict:
+def cpu_baseline(w, budget_s: float = 10.0, gpu_sample=None, configs_sample=None, budget_gammas=None) -> dict:
     """The oracle on whole slots of the workload (independent draws) until
     about budget_s seconds of wall time have been spent, all host cores; then
     on one core, on the leading channels of one slot, doubled until one run
@@ -295,7 +295,7 @@ def cpu_baseline(w, budget_s: float = 10.0, gpu_sample=None, configs_sample=None
                   "note": "where l matches; the GPU parity tests treat l differences (near-ties)"}
         # the exact bounded-alphabet minimum (depth-first sphere encoder) on 4 vectors of each channel
         tau = O.default_tau(w.qam)
-        ratios = []
+        ratios, vs, gmins = [], [], []
         for c in chans:
             f = O.factor_channel(b.H[c].astype(np.complex128), 1)
             if f["status"] != 0:
@@ -304,7 +304,16 @@ def cpu_baseline(w, budget_s: float = 10.0, gpu_sample=None, configs_sample=None
                 vl = O.qam_points(w.qam, b.sym[v])[f["user_of_level"]]
                 g_min, _ = O.sphere_min(f["Rt"], vl, tau)
                 ratios.append(g[v] / g_min)
+                vs.append(v)
+                gmins.append(g_min)
         r = np.asarray(ratios)
+        if budget_gammas and vs:
+            gm = np.asarray(gmins)
+            parity["exact_minimum_by_paths"] = {
+                str(n): {"reach_frac": float(np.mean(gg[vs] / gm <= 1.0 + 1e-5)),
+                         "gamma_over_min_mean": float(np.mean(gg[vs] / gm)),
+                         "gamma_over_min_max": float(np.max(gg[vs] / gm))}
+                for n, gg in sorted(budget_gammas.items())}
         if r.size:
             parity["exact_minimum"] = {
                 "vectors": int(r.size), "reach_frac": float(np.mean(r <= 1.0 + 1e-5)),
@@ -728,6 +737,43 @@ def measure_configs(dev, flush, steps: int, c1_draws: int = 16):
     return lines, outs
 
 
+def measure_path_budgets(dev, b, w, flush, steps: int, budgets=(16, 64, 256, 1024)) -> tuple:
+    """The benchmark slot at other path budgets n: vp_factorize + vp_precode
+    per slot (device-resident, L2 flushed between steps) and gamma of every
+    vector, for the oracle leg's comparison with the exact minimum. Returns
+    (lines, {n: gamma})."""
+    import numpy as np
+    import torch
+
+    import paper_2602_12098_gb300 as vp
+    stream = torch.cuda.current_stream()
+    C, K, M = b.H.shape
+    V, S = b.sym.shape[0], w.symbols
+    H, sym = torch.from_numpy(b.H).to(dev), torch.from_numpy(b.sym).to(dev)
+    x = torch.empty((V, M), dtype=torch.complex64, device=dev)
+    l = torch.empty((V, K, 2), dtype=torch.int8, device=dev)
+    g = torch.empty((V,), dtype=torch.float32, device=dev)
+    lines, gammas = [], {}
+    for n in budgets:
+        ts = []
+        with vp.Plan(K, M, w.qam, n) as plan:
+            for it in range(steps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vp.vp_factorize(plan.handle, H, C, stream=stream)
+                vp.vp_precode(plan.handle, sym, S, None, V, x, l, g, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= 3:
+                    ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        gammas[n] = g.cpu().numpy().astype(np.float64)
+        lines.append({"n_paths": n, "slot_ms": ms, "vectors_per_s": V / (ms / 1e3),
+                      "gamma_mean": float(gammas[n].mean())})
+    return lines, gammas
+
+
 def measure_paper_points(dev, flush, steps: int) -> list:
     """The shapes of the paper's FPGA throughput table (K = M = 4, 8, 12, 16,
     16-QAM) as whole slots with 8 paths: vectors/s of vp_factorize +
@@ -1070,6 +1116,7 @@ def run_gpu(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches[0], "clocks": clocks}
     plan.close()
     configs_out = None
+    budget_gammas = None
     if ws == 1 and not args.no_batched:
         line["demap_lut"] = measure_lut(dev, b, w, flush, min(args.steps, 100))
         line["fixed_point"] = measure_fixed(dev, b, w, flush, min(args.steps, 20))
@@ -1077,6 +1124,7 @@ def run_gpu(args):
         line["batched_one_vector"] = measure_batched(dev, flush, symbols_per_problem=1)
         line["paper_points"] = measure_paper_points(dev, flush, min(args.steps, 50))
         line["configs"], configs_out = measure_configs(dev, flush, min(args.steps, 50))
+        line["path_budgets"], budget_gammas = measure_path_budgets(dev, b, w, flush, min(args.steps, 20))
         line["pipelined"] = measure_pipelined(dev, w, min(args.steps, 200))
     if ws == 1 and not args.no_serving:
         line["serving"] = measure_serving(dev, args.serving_slots, args.serving_lanes, args.serving_pool_mib,
@@ -1084,7 +1132,7 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, gpu_sample=(b, x.cpu().numpy(), l.cpu().numpy(),
                                                            g.cpu().numpy().astype(np.float64)),
-                                            configs_sample=configs_out)
+                                            configs_sample=configs_out, budget_gammas=budget_gammas)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
