@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--subcarriers", type=int, default=None,
                     help="run a reduced slot (profiling captures); the default is the full slot")
+    ap.add_argument("--paths", type=int, default=None,
+                    help="candidate paths per vector instead of the workload's (the default is its own)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
     ap.add_argument("--serving-slots", type=int, default=2000)
@@ -183,6 +185,9 @@ def run_reference(args):
     from oracle import oracle as O
     from paper_2602_12098_gb300 import workloads as W
     w = W.WORKLOADS[args.workload]
+    if args.paths is not None:
+        import dataclasses
+        w = dataclasses.replace(w, n_paths=args.paths)
     threads = os.cpu_count() or 1
     O.build()
     # calibrate: how many channels fit a per-step budget so K + W steps take ~2 minutes
@@ -973,6 +978,9 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = W.WORKLOADS[args.workload]
+    if args.paths is not None:
+        import dataclasses
+        w = dataclasses.replace(w, n_paths=args.paths)
     b = replica_batch(w, rank, args.subcarriers)
     C, K, M = b.H.shape
     V = b.sym.shape[0]
@@ -1082,7 +1090,8 @@ def run_gpu(args):
     fp64_frac = float((stt.cpu().numpy() & vp.VP_CH_FP64).astype(bool).mean())
     exec_flops = 8.0 * executed_cmul(codes.cpu().numpy().view(np.uint64), K, M, w.n_paths) * V
     executed = exec_flops / (search_avg / 1e3) / 1e12
-    tr = profiled_traffic("search_kernel_slot16x16.md") if args.subcarriers is None else None
+    tr = (profiled_traffic("search_kernel_slot16x16.md")
+          if args.subcarriers is None and args.paths is None and args.workload == "slot_16x16" else None)
     roofline = {"bound": "alu", "kernel": "search_kernel<16> (vp_precode)", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "traffic": tr["bytes"] if tr else None,
