@@ -12,7 +12,8 @@
 //   and U) passes the plan threshold are redone with FP64: the Gram matrix
 //   (compensated FP32 sums, exact for FP32 input), pivoted reverse Cholesky
 //   with the same min-pivot rule, U = R^-1 and one Newton step
-//   U <- U (2I - R U) in FP64, then P = H^H U^H U as a hi/lo FP32 pair.
+//   U <- U (2I - R U) (the residual I - R U in FP64, the small correction
+//   U (I - R U) in FP32), then P = H^H U^H U as a hi/lo FP32 pair.
 //
 // Outputs per channel (level order unless noted): U~ = U_lk / U_ll (unit
 // upper), w_l = U_ll^2, the user of each level, and P^T in user order.
@@ -181,16 +182,29 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     const bool act = j < K;
     Smem32<MT>& sm = smem[slot];
 
-    // column j of A = H^H
+    // column j of A = H^H (row j of H, read as 16-byte pairs of entries when
+    // the rows are 16-byte aligned)
     float2 av[MT];
     bool finite = true;
+    const bool v4 = ((M & 1) == 0) && ((reinterpret_cast<uintptr_t>(f.H) & 15u) == 0u);
 #pragma unroll
-    for (int m = 0; m < MT; ++m) {
-        float2 h = make_float2(0.f, 0.f);
-        if (valid && act && m < M) h = f.H[j * M + m];
-        finite = finite && isfinite(h.x) && isfinite(h.y);
-        av[m] = make_float2(h.x, -h.y);
+    for (int m = 0; m < MT; m += 2) {
+        float2 h0 = make_float2(0.f, 0.f), h1 = h0;
+        if (valid && act && m < M) {
+            if (v4) {
+                const float4 q = *reinterpret_cast<const float4*>(f.H + j * M + m);
+                h0 = make_float2(q.x, q.y);
+                h1 = make_float2(q.z, q.w);
+            } else {
+                h0 = f.H[j * M + m];
+                if (m + 1 < M) h1 = f.H[j * M + m + 1];
+            }
+        }
+        finite = finite && isfinite(h0.x) && isfinite(h0.y) && isfinite(h1.x) && isfinite(h1.y);
+        av[m] = make_float2(h0.x, -h0.y);
+        if (m + 1 < MT) av[m + 1] = make_float2(h1.x, -h1.y);
         if (act && m == M + j && a.lambda > 0.f) av[m] = make_float2(a.lambda, 0.f);   // Hbar = [H lambda*I]
+        if (act && m + 1 == M + j && a.lambda > 0.f && m + 1 < MT) av[m + 1] = make_float2(a.lambda, 0.f);
     }
     const bool nonfinite = (__ballot_sync(kFull, !finite) & hmask) != 0u;
     if (nonfinite) {
@@ -499,24 +513,25 @@ __global__ void __launch_bounds__(NT) factor64_kernel(FactorArgs a)
             // diagonal NaN the winner is an inactive lane (ku not a user): singular
             if (ku < 0 || ku >= K || kp >= m || !(key > 1e-12 * dmax)) { singular = true; break; }   // uniform
             const int p = ku;
-            // 1 / sqrt(key): FP32 estimate, two Newton steps in FP64 (y <- y (3 - k y^2) / 2,
-            // each doubling the correct bits), then sqrt(key) = key / sqrt(key)
-            double irt = (double)rsqrtf((float)key);
-            if (!(irt > 0.0 && irt < INFINITY)) irt = 1.0 / sqrt(key);   // key outside the FP32 range
-            irt = irt * (1.5 - 0.5 * key * irt * irt);
-            irt = irt * (1.5 - 0.5 * key * irt * irt);
-            const double rt = key * irt;
             // remove p from the remaining list (move the last one into its position)
             const int last = sm.rem[m - 1];
             gsync();
             if (tid == 0) {
+                // 1 / sqrt(key): FP32 estimate, two Newton steps in FP64 (y <- y (3 - k y^2) / 2,
+                // each doubling the correct bits), then sqrt(key) = key / sqrt(key); one thread
+                // only, since the FP64 pipe is the contended unit of this kernel
+                double irt = (double)rsqrtf((float)key);
+                if (!(irt > 0.0 && irt < INFINITY)) irt = 1.0 / sqrt(key);   // key outside the FP32 range
+                irt = irt * (1.5 - 0.5 * key * irt * irt);
+                irt = irt * (1.5 - 0.5 * key * irt * irt);
                 sm.rem[kp] = last;
-                sm.rd[t] = rt;
+                sm.rd[t] = key * irt;
                 sm.rinv[t] = irt;
                 sm.uol[t] = p;
             }
             gsync();
             if (tid < m - 1) {
+                const double irt = sm.rinv[t];
                 const double2 v = sm.s[sm.rem[tid]][p];
                 const double2 l = make_double2(v.x * irt, v.y * irt);
                 sm.pc[tid] = l;
@@ -560,13 +575,17 @@ __global__ void __launch_bounds__(NT) factor64_kernel(FactorArgs a)
                 }
                 gsync();
             }
-            // one Newton step: E = I - R U, U2 = U + U E (both upper triangular), accumulated by rank-1 steps
+            // one Newton step U2 = U (2I - R U) = U + U E with E = I - R U (both upper
+            // triangular): E in FP64, accumulated by rank-1 steps (E_ik -= R_im U_mk,
+            // i <= m <= k); E is of the order of the FP64 rounding of U, so the
+            // correction U E is formed in FP32 (its rounding is far below U2's own), in
+            // the scratch arrays of the hi / lo parts: U in uh, E in ul, U E in ahi
             for (int e = tid; e < K * K; e += NT) {
                 const int r = e / K, q = e % K;
                 sm.s[r][q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
             }
             gsync();
-            for (int m = 0; m < K; ++m) {                               // E_ik -= R_im U_mk, i <= m <= k
+            for (int m = 0; m < K; ++m) {
                 const int w = K - m;
                 for (int e = tid; e < (m + 1) * w; e += NT) {
                     const int i = e / w, k = m + e % w;
@@ -576,16 +595,28 @@ __global__ void __launch_bounds__(NT) factor64_kernel(FactorArgs a)
                 }
                 gsync();
             }
-            for (int e = tid; e < K * K; e += NT) sm.lc[e / K][e % K] = sm.u[e / K][e % K];
-            gsync();
-            for (int m = 0; m < K; ++m) {                               // U2_ik += U_im E_mk, i <= m <= k
-                const int w = K - m;
-                for (int e = tid; e < (m + 1) * w; e += NT) {
-                    const int i = e / w, k = m + e % w;
-                    sm.lc[i][k] = zfma(sm.u[i][m], sm.s[m][k], sm.lc[i][k]);
-                }
-                gsync();
+            for (int e = tid; e < K * (K + 1) / 2; e += NT) {
+                int k, i;
+                tri_index(e, k, i);                                     // i <= k
+                sm.ul[i][k] = make_float2((float)sm.s[i][k].x, (float)sm.s[i][k].y);
+                sm.uh[i][k] = make_float2((float)sm.u[i][k].x, (float)sm.u[i][k].y);
             }
+            gsync();
+            for (int e = tid; e < K * (K + 1) / 2; e += NT) {
+                int k, i;
+                tri_index(e, k, i);
+                float2 c = make_float2(0.f, 0.f);
+                for (int m = i; m <= k; ++m) c = cfma(sm.uh[i][m], sm.ul[m][k], c);
+                sm.ahi[i][k] = c;
+            }
+            gsync();
+            for (int e = tid; e < K * K; e += NT) {                    // U2 (upper), in lc
+                const int r = e / K, q = e % K;
+                const double2 v = sm.u[r][q];
+                sm.lc[r][q] = (q >= r) ? make_double2(v.x + (double)sm.ahi[r][q].x, v.y + (double)sm.ahi[r][q].y)
+                                       : make_double2(0.0, 0.0);
+            }
+            gsync();
             // U2 (in lc) as FP32 hi + lo; outputs: row r of U~, w_r, user of level r
             if (tid < K) sm.rd[tid] = 1.0 / sm.lc[tid][tid].x;     // 1 / U2_rr
             gsync();
