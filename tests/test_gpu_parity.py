@@ -169,6 +169,38 @@ def test_edge_cases(orc):
     assert st["n_l_diff"] == 0 and st["x_err_max"] <= 1e-6, st
 
 
+def test_empty_inputs(orc):
+    """n_vec = 0 is a no-op that leaves the outputs untouched; channels with
+    no vectors (every channel but one, and a ragged tail) give the oracle's
+    results for the vectors that exist."""
+    dev = torch.device("cuda:0")
+    rng = W.rng_for(72, 0)
+    K = M = 8
+    C = 37                                   # 2 search tiles of channels plus a ragged tail
+    H = W.channels(rng, C, K, M)
+    x = torch.full((4, M), complex(7.0, 7.0), dtype=torch.complex64, device=dev)
+    l = torch.full((4, K, 2), 99, dtype=torch.int8, device=dev)
+    g = torch.full((4,), 5.0, dtype=torch.float32, device=dev)
+    sym = torch.zeros((4, K), dtype=torch.uint8, device=dev)
+    with vp.Plan(K, M, 64, 64) as plan:
+        vp.vp_factorize(plan.handle, torch.from_numpy(H).to(dev), C)
+        vp.vp_precode(plan.handle, sym, 0, torch.zeros(C + 1, dtype=torch.int32, device=dev), 0, x, l, g)
+        vp.vp_precode(plan.handle, sym, 0, None, 0, x, l, g)
+        with pytest.raises(vp.VPError) as e:           # S per channel must agree with n_vec
+            vp.vp_precode(plan.handle, sym, 3, None, 0, x, l, g)
+        assert e.value.code == 1
+        torch.cuda.synchronize()
+    assert torch.all(x == complex(7.0, 7.0)) and torch.all(l == 99) and torch.all(g == 5.0)
+    for counts in (np.r_[np.zeros(C - 1, dtype=int), 3], np.r_[2, np.zeros(C - 2, dtype=int), 1]):
+        off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        symn = W.symbols(rng, int(off[-1]), K, 64)
+        gpu = run_gpu(H, symn, off, 64, 64)
+        ref = oracle_run(orc, H, symn, off, 64, 64)
+        st = compare(orc, H, symn, off, 64, gpu, ref)
+        assert st["n_l_diff"] == 0, st
+        assert_parity(st)
+
+
 def test_host_buffer_slot_equals_device_path():
     b = W.make_batch(W.SLOT_16x16, subcarriers=64)
     wl = b.workload
