@@ -112,37 +112,41 @@ __device__ __forceinline__ void write_channel_outputs_zero(const FChan& f, int K
 // that converge from below). The two iterations are independent and run
 // interleaved, each with its own operations in its own order. Every lane of
 // the warp calls it; lane j < K holds component j of the iterates; K <= KT.
+// The iterates are exchanged through the channel's scratch rows `xv`
+// (rows 0-3: v_A, v_B, w_A, w_B), read back as shared-memory broadcasts.
 template <int KT>
-__device__ void power_sigma2_pair(const float2 (*A)[kRow32], const float2 (*B)[kRow32], int K, int j, float& la,
-                                  float& lb)
+__device__ void power_sigma2_pair(const float2 (*A)[kRow32], const float2 (*B)[kRow32], float2 (*xv)[kMaxK], int K,
+                                  int j, float& la, float& lb)
 {
     const bool act = j < K;
     float2 va = make_float2(act ? 1.f + 0.0625f * (float)j : 0.f, 0.f), vb = va;
     la = 0.f;
     lb = 0.f;
     for (int it = 0; it < 6; ++it) {
+        if (act) {
+            xv[0][j] = va;
+            xv[1][j] = vb;
+        }
+        __syncwarp(kFull);
         float2 wa = make_float2(0.f, 0.f), wb = wa;              // w = A v
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
-            if (k < K) {
-                const float2 vak = make_float2(__shfl_sync(kFull, va.x, k, kLanes), __shfl_sync(kFull, va.y, k, kLanes));
-                const float2 vbk = make_float2(__shfl_sync(kFull, vb.x, k, kLanes), __shfl_sync(kFull, vb.y, k, kLanes));
-                if (act && k >= j) {
-                    wa = cfma(A[j][k], vak, wa);
-                    wb = cfma(B[j][k], vbk, wb);
-                }
+            if (k < K && act && k >= j) {
+                wa = cfma(A[j][k], xv[0][k], wa);
+                wb = cfma(B[j][k], xv[1][k], wb);
             }
         }
+        if (act) {
+            xv[2][j] = wa;
+            xv[3][j] = wb;
+        }
+        __syncwarp(kFull);
         float2 za = make_float2(0.f, 0.f), zb = za;              // z = A^H w
 #pragma unroll
         for (int i = 0; i < KT; ++i) {
-            if (i < K) {
-                const float2 wai = make_float2(__shfl_sync(kFull, wa.x, i, kLanes), __shfl_sync(kFull, wa.y, i, kLanes));
-                const float2 wbi = make_float2(__shfl_sync(kFull, wb.x, i, kLanes), __shfl_sync(kFull, wb.y, i, kLanes));
-                if (act && i <= j) {
-                    za = cfma(make_float2(A[i][j].x, -A[i][j].y), wai, za);
-                    zb = cfma(make_float2(B[i][j].x, -B[i][j].y), wbi, zb);
-                }
+            if (i < K && act && i <= j) {
+                za = cfma(make_float2(A[i][j].x, -A[i][j].y), xv[2][i], za);
+                zb = cfma(make_float2(B[i][j].x, -B[i][j].y), xv[3][i], zb);
             }
         }
         float nwa = cabs2(wa), nva = cabs2(va), nza = cabs2(za);
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     // cond(H H^H) = (sigma_max(R) sigma_max(U))^2, estimated by power iteration;
     // channels above the plan threshold (or degenerate) go to the FP64 path
     float sr, su;
-    power_sigma2_pair<KT>(sm.rl, sm.uu, K, j, sr, su);
+    power_sigma2_pair<KT>(sm.rl, sm.uu, sm.ru, K, j, sr, su);    // ru is free after R's level order
     const float kappa = sr * su;
     const bool degen = (__ballot_sync(kFull, degenerate) & hmask) != 0u;
     const float thr = (a.probs && valid) ? a.probs[c].kappa_thr : a.kappa_thr;
@@ -339,17 +343,18 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
     }
 
     if (act) {
-        const int i = j;
-        const float rii = sm.rl[i][i].x;
-        const float uii = sm.uu[i][i].x;
-        f.s.w[i] = uii * uii;
-        const uint8_t ui = (uint8_t)sm.piv[K - 1 - i];
-        f.s.ul[i] = ui;
-        if (f.ul_out) f.ul_out[i] = ui;
-        for (int k = 0; k < K; ++k) {
-            float2 u = sm.uu[i][k];
-            float2 ut = (k > i) ? make_float2(u.x * rii, u.y * rii)
-                                : (k == i ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
+        const float uii = sm.uu[j][j].x;
+        f.s.w[j] = uii * uii;
+        const uint8_t ui = (uint8_t)sm.piv[K - 1 - j];
+        f.s.ul[j] = ui;
+        if (f.ul_out) f.ul_out[j] = ui;
+        // lane k writes column k of each row i (row-major stores coalesced across the lanes)
+        const int k = j;
+        for (int i = 0; i < K; ++i) {
+            const float rii = sm.rl[i][i].x;
+            const float2 u = sm.uu[i][k];
+            const float2 ut = (k > i) ? make_float2(u.x * rii, u.y * rii)
+                                      : (k == i ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
             f.s.utp[i * K + k] = make_float4(ut.x, ut.y, ut.y, ut.x);
             f.s.utc[k * K + i] = ut;
             if (f.U_out) f.U_out[i * K + k] = u;
