@@ -262,12 +262,11 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
 #pragma unroll
                 for (int m = 0; m < MT; ++m) sm.refl[t][m] = vv[m];
             }
+            // the reflector reaches the other lanes as shared-memory broadcasts
+            __syncwarp(kFull);
 #pragma unroll
-            for (int m = t; m < MT; ++m) {
-                vv[m].x = __shfl_sync(kFull, vv[m].x, p, kLanes);
-                vv[m].y = __shfl_sync(kFull, vv[m].y, p, kLanes);
-            }
-            beta = __shfl_sync(kFull, beta, p, kLanes);
+            for (int m = t; m < MT; ++m) vv[m] = sm.refl[t][m];
+            beta = sm.beta[t];
             if (!placed) {
                 float2 s = make_float2(0.f, 0.f);
 #pragma unroll
