@@ -174,6 +174,7 @@ template <int MT, int KT>
 __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(FactorArgs a)
 {
     __shared__ Smem32<MT> smem[kChPerBlock32];
+    pdl_wait();
     const int slot = threadIdx.x / kLanes;
     const int j = threadIdx.x % kLanes;
     const int hw = (threadIdx.x >> 4) & 1;                 // half of the warp
@@ -395,6 +396,7 @@ __global__ void __launch_bounds__(kLanes * kChPerBlock32) factor32_kernel(Factor
         }
     }
     if (j == 0) f.s.st[0] = 0;
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
@@ -458,6 +460,7 @@ __global__ void __launch_bounds__(NT) factor64_kernel(FactorArgs a)
 {
     __shared__ Smem64 sm;
     const int tid = threadIdx.x, lane = threadIdx.x & 31;
+    pdl_wait();                                    // the flag list of the FP32 factor
     const int nflag = *a.nflag_in;
     auto gsync = [&]() { if (NT == 32) __syncwarp(); else __syncthreads(); };
 
@@ -698,6 +701,7 @@ __global__ void __launch_bounds__(NT) factor64_kernel(FactorArgs a)
         }
         gsync();
     }
+    pdl_trigger();
 }
 
 FactorArgs make_args(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out, uint8_t* ul_out)
@@ -746,8 +750,7 @@ cudaError_t run_factor64(const FactorArgs& a, int max_flagged, cudaStream_t s)
     int blocks = max_flagged;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    factor64_kernel<kNT64><<<blocks, kNT64, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(factor64_kernel<kNT64>, dim3(blocks), dim3(kNT64), 0, s, a);
 }
 
 }  // namespace

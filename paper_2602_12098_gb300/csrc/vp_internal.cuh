@@ -196,6 +196,36 @@ cudaError_t enqueue_slot(const vp_plan* p, const float2* H, int C, const uint8_t
 // default 48 KB.
 cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes);
 
+// Programmatic dependent launch: a kernel launched by launch_dependent may
+// be scheduled while the kernel before it on the stream is still running
+// (once every block of that kernel has called pdl_trigger or exited), so its
+// launch and block start-up overlap the predecessor's last blocks. Every
+// kernel calls pdl_wait before it reads anything that earlier work on the
+// stream produced (it returns once the predecessor grid has completed and
+// its writes are visible; without the launch attribute it returns at once),
+// and pdl_trigger when its block's work is done: after the wait, so that
+// completion is transitive along a chain of such launches, and late, since
+// dependent blocks waiting beside the kernel's own work slowed it down.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Kernel launchers (each returns cudaSuccess or the launch error).
 cudaError_t launch_factor32(const vp_plan* p, const float2* H, int C, float2* U_out, float2* P_out,
                             uint8_t* ul_out, cudaStream_t s);

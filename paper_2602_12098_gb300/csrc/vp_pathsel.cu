@@ -341,6 +341,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
     extern __shared__ uint64_t shm[];
     __shared__ uint64_t qws[8][kMaxK];
     __shared__ int ords[8][kMaxK];
+    pdl_wait();                                                  // weights and status of the factor kernels
     const int tpc = blockDim.x / cpb;                            // threads per channel
     const int grp = threadIdx.x / tpc, t = threadIdx.x % tpc;
     const int lane = threadIdx.x & 31, wig = t >> 5;             // lane, warp within the channel's group
@@ -425,6 +426,7 @@ __global__ void pathsel_kernel(PathArgs a, int cpb)
 #undef BC
     for (int i = t; i < n; i += tpc) out[i] = (i < s) ? Sc[sk(i)] : 0;
     eval_order(cs, out, base, n, K, nch, t, tpc);
+    pdl_trigger();
 }
 
 cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s, int tpc_set = 0)
@@ -446,8 +448,7 @@ cudaError_t run_pathsel(PathArgs a, int n_max, cudaStream_t s, int tpc_set = 0)
     const size_t shbytes = per * cpb;
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(pathsel_kernel), shbytes);
     if (e != cudaSuccess) return e;
-    pathsel_kernel<<<(a.C + cpb - 1) / cpb, tpc * cpb, shbytes, s>>>(a, cpb);
-    return cudaGetLastError();
+    return launch_dependent(pathsel_kernel, dim3((a.C + cpb - 1) / cpb), dim3(tpc * cpb), shbytes, s, a, cpb);
 }
 
 }  // namespace

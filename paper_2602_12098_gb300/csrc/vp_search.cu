@@ -599,7 +599,9 @@ template <int KT, bool BATCH, bool LUT, bool FIX, bool GP, bool TC>
 __global__ void __launch_bounds__(224, 4) search_kernel(SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();                                // paths and factors of the kernels before
     search_block<KT, BATCH, LUT, FIX, GP, TC>(a, blockIdx.x, smraw);
+    pdl_trigger();
 }
 
 // One problem of a persistent launch, as its own function (each K tile keeps
@@ -620,6 +622,8 @@ __global__ void __launch_bounds__(224, 4) search_persist_kernel(SearchArgs a, in
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int item;
+    pdl_wait();
+    pdl_trigger();
     for (;;) {
         if (threadIdx.x == 0) item = atomicAdd(counter, 1);
         __syncthreads();
@@ -671,6 +675,8 @@ __global__ void __launch_bounds__(224, 4) search_small_kernel(SearchArgs a)
 {
     constexpr int P = 32 / G;
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     const int NW = blockDim.x >> 5;
     const int c = blockIdx.x;
     const int K = a.K, M = a.M, Mp = a.Mp, n = a.n, m_qam = a.m_qam;
@@ -834,8 +840,7 @@ cudaError_t launch_small(const SearchArgs& a, int C, int per, cudaStream_t s)
     const size_t sh = (size_t)small_smem(KT, a.K * a.Mp, nw, G).total;
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_small_kernel<KT, G>), sh);
     if (e != cudaSuccess) return e;
-    search_small_kernel<KT, G><<<C, nw * 32, sh, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(search_small_kernel<KT, G>, dim3(C), dim3(nw * 32), sh, s, a);
 }
 
 template <int KT>
@@ -852,8 +857,7 @@ cudaError_t launch_one(const SearchArgs& a, int C, int threads, int KM, int NP, 
     const size_t sh = (size_t)search_smem(KT, KM, NP, threads / 32, GP, TC, a.Mp).total;
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(search_kernel<KT, BATCH, LUT, FIX, GP, TC>), sh);
     if (e != cudaSuccess) return e;
-    search_kernel<KT, BATCH, LUT, FIX, GP, TC><<<C, threads, sh, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(search_kernel<KT, BATCH, LUT, FIX, GP, TC>, dim3(C), dim3(threads), sh, s, a);
 }
 
 // Paths read in place (GP) where staging them would cost occupancy: only the
