@@ -31,7 +31,12 @@
  *
  * Streams. `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream). Calls enqueue work and return without synchronising,
- * except where noted.
+ * except where noted. Stream order holds as usual: work the caller enqueues
+ * before a call is complete before the call's kernels read their inputs,
+ * and work enqueued after a call starts after the call's kernels end. (The
+ * library's own kernels after the first of vp_factorize use programmatic
+ * dependent launch, which only lets their launch overlap the end of the
+ * kernel before them.)
  *
  * Errors. Argument errors are returned synchronously and nothing is
  * enqueued. Launch failures return VP_ERR_CUDA. Per-channel numerical
